@@ -1,0 +1,374 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix (no GPU).
+
+Each test ties one oracle function to something other than itself: the printed stencil
+and W_Diri formula, a dense direct solve of the all-at-once system, the separable modal
+closed form, the printed lambda_eff values, a dense Kronecker-product brute-force V-cycle,
+the adjoint identity, central finite differences, and the paper's qualitative claims.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import dense
+from paper_2505_10168_gb300 import workloads as wl
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _gold(name):
+    with open(os.path.join(GOLD, name)) as f:
+        return json.load(f)
+
+
+def _rand_material(seed, N, contrast=1e3):
+    u = wl.uniform(seed, 2 * N)
+    k = np.exp(np.log(1.0 / contrast) * u[:N])
+    c = 0.5 + u[N:]
+    return k, c
+
+
+def _rand_vec(seed, shape):
+    return wl.uniform(seed, int(np.prod(shape))).reshape(shape) - 0.5
+
+
+# ---------------------------------------------------------------- assembly (Sec. 2.2, App. A)
+
+def test_interior_stencil_matches_printed_stencil():
+    g = _gold("stencil_sec2.json")
+    N, NT, L, tT, kc, cc = 8, 8, 1.3, 0.9, 0.7, 1.9
+    H = oracle.Hierarchy(N, NT, L, tT, np.full(N, kc), np.full(N, cc), num_levels=1)
+    dx, dt = L / N, tT / NT
+    expect = cc * dx / dt * np.array(g["mass"]) + kc / dx * np.array(g["stiffness"])
+    n, i = 4, 4
+    row = np.zeros((NT + 1, N + 1))
+    for m in range(NT + 1):
+        for j in range(N + 1):
+            e = np.zeros((NT + 1, N + 1))
+            e[m, j] = 1.0
+            row[m, j] = H.apply(0, e)[n, i]
+    got = np.array([[row[n + 1, i - 1], row[n + 1, i], row[n + 1, i + 1]],
+                    [row[n, i - 1], row[n, i], row[n, i + 1]],
+                    [row[n - 1, i - 1], row[n - 1, i], row[n - 1, i + 1]]])
+    np.testing.assert_allclose(got, expect, rtol=1e-14, atol=1e-12)
+    row[n - 1:n + 2, i - 1:i + 2] = 0.0
+    assert np.all(row == 0.0), "J has entries outside the 6-point stencil"
+
+
+def test_dirichlet_weight_formula():
+    N, NT, L, tT = 6, 5, 2.0, 3.0
+    k, c = _rand_material(11, N)
+    H = oracle.Hierarchy(N, NT, L, tT, k, c, num_levels=1)
+    W = c.max() * (L / N) / (tT / NT) + k.max() / (L / N)
+    for (m, j) in [(0, 0), (0, 3), (2, 0), (NT, 0)]:
+        e = np.zeros((NT + 1, N + 1))
+        e[m, j] = 1.0
+        y = H.apply(0, e)
+        assert y[m, j] == pytest.approx(W, rel=1e-15)
+        y[m, j] = 0.0
+        assert np.all(y == 0.0)  # Dirichlet columns are eliminated
+
+
+@pytest.mark.parametrize("N,NT", [(2, 2), (4, 8), (8, 4), (5, 3), (1, 6)])
+def test_operator_matches_dense_all_at_once(N, NT):
+    L, tT = 1.7, 0.6
+    k, c = _rand_material(N * 31 + NT, N)
+    H = oracle.Hierarchy(N, NT, L, tT, k, c, num_levels=1)
+    J = dense.all_at_once(N, NT, L, tT, k, c)
+    u = _rand_vec(5, (NT + 1, N + 1))
+    scale = np.abs(J).max() * np.abs(u).max()
+    np.testing.assert_allclose(H.apply(0, u).ravel(), J @ u.ravel(), rtol=0, atol=1e-14 * scale)
+    np.testing.assert_allclose(H.apply(0, u, adj=True).ravel(), J.T @ u.ravel(), rtol=0, atol=1e-14 * scale)
+    np.testing.assert_allclose(H.diag(0).ravel(), np.diag(J), rtol=1e-15)
+
+
+def test_load_vector_matches_dense():
+    N, NT, L = 7, 5, 1.4
+    q = _rand_vec(3, (NT + 1, N)) + 2.0
+    b = oracle.assemble_load(N, NT, L / N, q)
+    np.testing.assert_allclose(b.ravel(), dense.load_vector(N, NT, L / N, q), rtol=1e-15, atol=0)
+    assert np.all(b[0] == 0) and np.all(b[:, 0] == 0)
+
+
+# ---------------------------------------------------------------- exact solution
+
+@pytest.mark.parametrize("N,NT", [(2, 2), (4, 8), (8, 4), (3, 7)])
+@pytest.mark.parametrize("adj", [False, True])
+def test_exact_time_stepping_matches_dense_lu(N, NT, adj):
+    L, tT = 1.0, 2.0
+    k, c = _rand_material(N + 7 * NT, N, contrast=1e4)
+    J = dense.all_at_once(N, NT, L, tT, k, c)
+    b = _rand_vec(17, (NT + 1, N + 1))  # includes Dirichlet entries, as on coarse levels
+    u = oracle.exact(N, NT, L, tT, k, c, b, adj=adj)
+    ref = np.linalg.solve(J.T if adj else J, b.ravel())
+    np.testing.assert_allclose(u.ravel(), ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+
+
+def test_exact_matches_modal_closed_form():
+    """Constant k, c: v_j(i) = sin(theta_j i), theta_j = (2j-1) pi / (2N) are the generalized
+    eigenvectors of (K, M) on nodes 1..N with mu_j = 6k(1-cos th)/(c dx^2 (2+cos th)); the
+    backward-Euler recurrence is a_j(n) = (a_j(n-1) + dt g_j(n)) / (1 + dt mu_j)."""
+    N, NT, L, tT, kc, cc = 32, 64, 1.0, 0.5, 0.8, 1.3
+    dx, dt = L / N, tT / NT
+    q = wl.load_paper(N, NT, L, tT) * 1e-6
+    b = oracle.assemble_load(N, NT, dx, q)
+    u = oracle.exact(N, NT, L, tT, np.full(N, kc), np.full(N, cc), b)
+    i = np.arange(1, N + 1)
+    th = (2 * np.arange(1, N + 1) - 1) * np.pi / (2 * N)
+    V = np.sin(np.outer(i, th))  # columns v_j
+    mu = 6 * kc * (1 - np.cos(th)) / (cc * dx * dx * (2 + np.cos(th)))
+    M, _ = dense.global_mk(N, dx, np.full(N, kc), np.full(N, cc))
+    Mi = M[1:, 1:]
+    nrm = np.einsum("ij,ik,kj->j", V, Mi, V)
+    a = np.zeros(N)
+    ref = np.zeros((NT + 1, N + 1))
+    for n in range(1, NT + 1):
+        g = V.T @ b[n, 1:] / nrm
+        a = (a + dt * g) / (1 + dt * mu)
+        ref[n, 1:] = V @ a
+    np.testing.assert_allclose(u, ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+
+
+# ---------------------------------------------------------------- planner (Alg. 3/4, Sec. 5.1)
+
+@pytest.mark.parametrize("prob", ["problem7", "problem8"])
+def test_lambda_eff_printed_values(prob):
+    g = _gold("lambda_eff_sec5.json")[prob]
+    p = wl.paper_problem(int(prob[-1]), tT=g["tT"])
+    k, c = oracle.simp(p["chi"], p["simp"])
+    H = oracle.Hierarchy(p["N"], p["NT"], p["L"], p["tT"], k, c, num_levels=1)
+    assert round(H.levels[0]["lambda_eff"], g["digits"]) == g["lambda_eff"]
+
+
+def test_alg3_path_uniform_material():
+    # k = c = 1, L = 1, N = 64, NT = 64, tT chosen so that lambda = 2 on level 1:
+    # x: 2 -> 0.5 -> 0.125 (< 0.25: t) -> 0.25 (not < 0.25: x) -> 0.0625 (t) -> 0.125 (t)
+    N = NT = 64
+    tT = 2.0 * NT / N ** 2
+    H = oracle.Hierarchy(N, NT, 1.0, tT, np.ones(N), np.ones(N), num_levels=7)
+    assert H.path() == "xxtxtt"
+    lam = [lv["lambda_eff"] for lv in H.levels]
+    np.testing.assert_allclose(lam, [2, 0.5, 0.125, 0.25, 0.0625, 0.125, 0.25], rtol=1e-14)
+
+
+def test_alg4_min_elements_forces_t():
+    N = NT = 64
+    tT = 2.0 * NT / N ** 2 * 64  # lambda = 128: pure x-coarsening under Alg. 3
+    H3 = oracle.Hierarchy(N, NT, 1.0, tT, np.ones(N), np.ones(N), num_levels=6)
+    H4 = oracle.Hierarchy(N, NT, 1.0, tT, np.ones(N), np.ones(N), num_levels=6, min_nel=16)
+    assert H3.path() == "xxxxx"
+    assert H4.path() == "xxttt"  # N/2 < 16 once N = 16
+
+
+def test_coarse_material_rules():
+    N, NT = 8, 4
+    k, c = _rand_material(21, N, contrast=1e5)
+    for reasm, expect in [("R", 2 * k[0::2] * k[1::2] / (k[0::2] + k[1::2])), ("K", (k[0::2] + k[1::2]) / 2)]:
+        H = oracle.Hierarchy(N, NT, 1.0, 1e-6, k, c, num_levels=2, reassembly=reasm, lambda_crit=0.0)
+        assert H.path() == "x"
+        np.testing.assert_allclose(H.levels[1]["k"], expect, rtol=1e-14)
+        np.testing.assert_allclose(H.levels[1]["c"], (c[0::2] + c[1::2]) / 2, rtol=1e-15)
+    H = oracle.Hierarchy(N, NT, 1.0, 1e-9, k, c, num_levels=2, lambda_crit=1e300)
+    assert H.path() == "t"
+    np.testing.assert_array_equal(H.levels[1]["k"], k)
+    assert H.levels[1]["dt"] == pytest.approx(2e-9 / NT * 1.0, rel=1e-15)
+
+
+def test_design_dependent_vs_fixed_deff():
+    p = wl.paper_problem(7, tT=10.0)
+    k, c = oracle.simp(p["chi"], p["simp"])
+    s = p["simp"]
+    deff = np.sqrt(s[0] / s[2] * s[1] / s[3])  # Sec. 7.2: sqrt(D_SIMP(0) D_SIMP(1))
+    Hf = oracle.Hierarchy(256, 256, p["L"], p["tT"], k, c, num_levels=6, deff_fixed=deff)
+    Hd = oracle.Hierarchy(256, 256, p["L"], p["tT"], k, c, num_levels=6)
+    assert Hf.levels[0]["lambda_eff"] == pytest.approx(Hd.levels[0]["lambda_eff"], rel=1e-12)
+    lam = [lv["lambda_eff"] for lv in Hf.levels]
+    for l, lv in enumerate(Hf.levels[:-1]):  # fixed D_eff: lambda scales only with dt/dx^2
+        f = 4.0 if lv["next"] == oracle.XCOARSEN else 0.5
+        assert lam[l + 1] == pytest.approx(lam[l] / f, rel=1e-14)
+
+
+# ---------------------------------------------------------------- transfer operators (Sec. 3.1)
+
+@pytest.mark.parametrize("kind", ["x", "t"])
+def test_prolong_restrict_match_kronecker(kind):
+    N, NT = 8, 8
+    k, c = _rand_material(4, N)
+    lc = 1e300 if kind == "t" else 0.0
+    H = oracle.Hierarchy(N, NT, 1.0, 1.0, k, c, num_levels=2, lambda_crit=lc)
+    assert H.path() == kind
+    P, s = dense.prolongation(N, NT, kind)
+    z = _rand_vec(8, H.shape(1))
+    u = _rand_vec(9, H.shape(0))
+    np.testing.assert_allclose(H.prolong_add(0, z, u).ravel(), u.ravel() + P @ z.ravel(), rtol=1e-15, atol=1e-15)
+    np.testing.assert_allclose(H.restrict(0, u).ravel(), s * P.T @ u.ravel(), rtol=1e-15, atol=1e-15)
+
+
+# ---------------------------------------------------------------- V-cycle (Alg. 1) vs dense brute force
+
+@pytest.mark.parametrize("N,NT,lam", [(8, 8, 2.0), (16, 8, 0.05), (8, 16, 0.3), (16, 16, 1.0)])
+@pytest.mark.parametrize("reasm", ["R", "K"])
+@pytest.mark.parametrize("adj", [False, True])
+def test_vcycle_matches_dense_bruteforce(N, NT, lam, reasm, adj):
+    k, c = _rand_material(N + NT, N, contrast=1e3)
+    deff = np.sqrt((k / c).min() * (k / c).max())
+    tT = lam * (1.0 / N) ** 2 / deff * NT
+    H = oracle.Hierarchy(N, NT, 1.0, tT, k, c, reassembly=reasm, max_coarse_dofs=20, nu=3)
+    path = H.path()
+    assert len(path) >= 2
+    D = dense.DenseHierarchy(N, NT, 1.0, tT, k, c, path, reassembly=reasm)
+    b = _rand_vec(31, H.shape(0))
+    u = np.zeros(H.shape(0))
+    ud = u.ravel().copy()
+    for cyc in range(3):
+        u = H.vcycle(u, b, adj=adj)
+        ud = D.vcycle(0, ud, b.ravel(), nu=3, adj=adj)
+        np.testing.assert_allclose(u.ravel(), ud, rtol=0, atol=1e-12 * np.abs(ud).max())
+
+
+def test_level_operators_match_dense_on_every_level():
+    N, NT = 16, 16
+    k, c = _rand_material(77, N, contrast=1e4)
+    H = oracle.Hierarchy(N, NT, 1.0, 0.02, k, c, max_coarse_dofs=10)
+    D = dense.DenseHierarchy(N, NT, 1.0, 0.02, k, c, H.path())
+    for l, lv in enumerate(D.levels):
+        u = _rand_vec(40 + l, H.shape(l))
+        np.testing.assert_allclose(H.apply(l, u).ravel(), lv["J"] @ u.ravel(), rtol=0,
+                                   atol=1e-13 * np.abs(lv["J"]).max())
+        assert H.levels[l]["W"] == pytest.approx(dense.w_diri(1.0 / lv["N"], 0.02 / lv["NT"], lv["k"], lv["c"]),
+                                                 rel=1e-13)
+
+
+# ---------------------------------------------------------------- solver loop and invariants
+
+def test_config1_converges_to_exact_solution():
+    cfg = wl.config1()
+    N, NT = cfg["N"], cfg["NT"]
+    H = oracle.Hierarchy(N, NT, cfg["L"], cfg["tT"], cfg["k"], cfg["c"])
+    b = oracle.assemble_load(N, NT, cfg["L"] / N, cfg["q"])
+    u, st, cyc, hist = H.solve(b, tol=1e-10)
+    assert st == "converged" and hist[-1] < 1e-10 and cyc < 40
+    ue = oracle.exact(N, NT, cfg["L"], cfg["tT"], cfg["k"], cfg["c"], b)
+    assert np.abs(u - ue).max() <= 1e-8 * np.abs(ue).max()
+    rho = (hist[-1] / hist[0]) ** (1.0 / cyc)  # Sec. 3.1 convergence factor estimate
+    assert rho < 0.6
+
+
+def test_linearity_of_the_cycle():
+    cfg = wl.config1()
+    N, NT = cfg["N"], cfg["NT"]
+    H = oracle.Hierarchy(N, NT, cfg["L"], cfg["tT"], cfg["k"], cfg["c"])
+    b = _rand_vec(3, H.shape(0))
+    u1 = H.vcycle(np.zeros(H.shape(0)), b)
+    u2 = H.vcycle(np.zeros(H.shape(0)), 1024.0 * b)  # power of two: scaling is exact
+    np.testing.assert_array_equal(u2, 1024.0 * u1)
+
+
+def test_adjoint_identity_and_cycle_counts():
+    cfg = wl.config4(N=64, NT=128)
+    N, NT = cfg["N"], cfg["NT"]
+    k, c = oracle.simp(cfg["chi"], cfg["simp"])
+    dt = cfg["tT"] / NT
+    b = oracle.assemble_load(N, NT, cfg["L"] / N, cfg["q"])
+    u = oracle.exact(N, NT, cfg["L"], cfg["tT"], k, c, b)
+    lam = oracle.exact(N, NT, cfg["L"], cfg["tT"], k, c, b * dt, adj=True)
+    theta = oracle.objective(N, NT, dt, b, u)
+    assert float(np.sum(lam * b)) == pytest.approx(theta, rel=1e-12)
+    H = oracle.Hierarchy(N, NT, cfg["L"], cfg["tT"], k, c)
+    _, s1, c1, _ = H.solve(b, tol=1e-10)
+    lam2, s2, c2, _ = H.solve(b * dt, adj=True, tol=1e-10)
+    assert s1 == s2 == "converged"
+    assert abs(c1 - c2) <= max(3, 0.3 * c1)  # Sec. 7.3: adjoint counts close to primal
+    assert np.abs(lam2 - lam).max() <= 1e-8 * np.abs(lam).max()
+
+
+@pytest.mark.parametrize("penalise_c", [False, True])
+def test_sensitivity_matches_central_differences(penalise_c):
+    N, NT, L, tT = 24, 40, 1.0, 1.0
+    chi = 0.1 + 0.8 * wl.uniform(12, N)
+    s = wl.simp_params(1e-3, 1.0, 0.3 if penalise_c else 1.0, 1.0)
+    q = wl.load_paper(N, NT, L, tT) * 1e-6
+    dt = tT / NT
+    b = oracle.assemble_load(N, NT, L / N, q)
+
+    def theta(x):
+        k, c = oracle.simp(x, s)
+        return oracle.objective(N, NT, dt, b, oracle.exact(N, NT, L, tT, k, c, b))
+
+    k, c = oracle.simp(chi, s)
+    u = oracle.exact(N, NT, L, tT, k, c, b)
+    lam = oracle.exact(N, NT, L, tT, k, c, b * dt, adj=True)
+    g = oracle.sensitivity(N, NT, L, tT, chi, s, u, lam)
+    # h = 1e-5: truncation error O(h^2) ~ 1e-10 relative, rounding noise ~ 100 eps Theta / h.
+    h = 1e-5
+    th0 = theta(chi)
+    for e in [0, 1, 5, 11, N - 2, N - 1]:
+        xp, xm = chi.copy(), chi.copy()
+        xp[e] += h
+        xm[e] -= h
+        fd = (theta(xp) - theta(xm)) / (2 * h)
+        assert g[e] == pytest.approx(fd, rel=1e-6, abs=100 * np.finfo(float).eps * th0 / h)
+
+
+def test_solver_reports_divergence_and_max_cycles():
+    cfg = wl.config1()
+    N, NT = cfg["N"], cfg["NT"]
+    b = oracle.assemble_load(N, NT, 1.0 / N, cfg["q"])
+    H = oracle.Hierarchy(N, NT, 1.0, 1.0, cfg["k"], cfg["c"], nu=1)
+    _, st, cyc, _ = H.solve(b, tol=1e-30, max_cycles=3)
+    assert st == "max_cycles" and cyc == 3
+    Hbad = oracle.Hierarchy(N, NT, 1.0, 1.0, cfg["k"], cfg["c"], omega=2.5)  # over-damped smoother
+    _, st, _, hist = Hbad.solve(b, tol=1e-10, div_tol=1e3)
+    assert st == "diverged" and hist[-1] > 1e3
+
+
+def test_zero_rhs_gives_zero():
+    H = oracle.Hierarchy(8, 8, 1.0, 1.0, np.ones(8), np.ones(8))
+    u, st, cyc, _ = H.solve(np.zeros(H.shape(0)))
+    assert st == "converged" and cyc == 0 and np.all(u == 0)
+
+
+def _two_grid_factor(N, NT, L, tT, k, c, kind):
+    lc = 1e300 if kind == "t" else 0.0
+    H = oracle.Hierarchy(N, NT, L, tT, k, c, num_levels=2, lambda_crit=lc, reassembly="K")
+    assert H.path() == kind
+    b = oracle.assemble_load(N, NT, L / N, wl.load_paper(N, NT, L, tT))
+    _, _, cyc, hist = H.solve(b, tol=1e-9, max_cycles=100)
+    return (hist[-1] / hist[0]) ** (1.0 / cyc)
+
+
+def test_two_grid_crossover_uniform_material():
+    """Sec. 3.2: t-coarsening wins for small lambda, x-coarsening for large, crossing near 0.1."""
+    g = _gold("coarsening_crossover.json")
+    N = NT = 64
+    rows = []
+    for p in [-6, -4, -2, 0, 2]:
+        lam = 2.0 ** p
+        tT = lam * NT / N ** 2
+        rows.append((lam, _two_grid_factor(N, NT, 1.0, tT, np.ones(N), np.ones(N), "x"),
+                     _two_grid_factor(N, NT, 1.0, tT, np.ones(N), np.ones(N), "t")))
+    for lam, fx, ft in rows:
+        if lam <= g["lambda_crit_uniform"] / 4:
+            assert ft < fx, (lam, fx, ft)
+        if lam >= g["lambda_crit_uniform"] * 4:
+            assert fx < ft, (lam, fx, ft)
+
+
+@pytest.mark.slow
+def test_two_grid_crossover_band_problem2():
+    """Sec. 4: for problem 2 the x/t curves cross inside 2^-3 <= lambda_eff <= 2^-1."""
+    g = _gold("coarsening_crossover.json")
+    lo, hi = g["band_log2"]
+    N = NT = 128
+    p = wl.paper_problem(2, N=N, NT=NT)
+    k, c = oracle.simp(p["chi"], p["simp"])
+    d = k / c
+    deff = np.sqrt(d.min() * d.max())
+    res = {}
+    for e in [lo - 2, hi + 2]:
+        tT = 2.0 ** e * (1.0 / N) ** 2 / deff * NT
+        res[e] = (_two_grid_factor(N, NT, 1.0, tT, k, c, "x"), _two_grid_factor(N, NT, 1.0, tT, k, c, "t"))
+    assert res[lo - 2][1] < res[lo - 2][0]  # below the band: t-coarsening better
+    assert res[hi + 2][0] < res[hi + 2][1]  # above the band: x-coarsening better
