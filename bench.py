@@ -1,0 +1,352 @@
+"""Benchmark: space-time DOF/s of a full STMG solve to 1e-8 relative residual.
+
+One step = one ``stmg_solve`` of the 4097 x 16385-node workload (N = 4096 elements,
+NT = 16384 steps, box-filtered SIMP conductivity with k_ins = 1e-4, heat load on
+x < 0.1) from u = 0 until ||J u - b|| / ||b|| < 1e-8, including the nodal load
+assembly from element loads already resident in HBM.  Hierarchy set-up is timed
+separately.  Every vector (537 MB in FP64) is larger than L2, so no flush is needed.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed]
+    python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores
+
+Under torchrun every rank solves its own copy (replicas, weak scaling) and rank 0
+prints one JSON line.  The roofline object is measured live on the dominant kernel.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "space-time DOF/s solved to 1e-8 rel. residual (HBM GB/s %); serving p50/p99"
+TOL = 1e-8
+NOMINAL_FP64_TFLOPS = 1.25  # GB300 FP64 (vector and tensor), nominal
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    p.add_argument("--workload", default="config2", choices=["config1", "config2", "config3", "config4"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def load_workload(name):
+    from paper_2505_10168_gb300 import workloads as wl
+
+    return getattr(wl, name)()
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples while the timed region runs."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu_id), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_smi_id(dev):
+    import torch
+
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return 0
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+def oracle_sample(w, nt_sample, tol=TOL):
+    """Oracle STMG solve of the first nt_sample time steps of the workload (same dx, dt,
+    material and load), timed on one host core."""
+    import oracle
+
+    N = w["N"]
+    if w["k"] is None:
+        k, c = oracle.simp(w["chi"], w["simp"])
+    else:
+        k, c = w["k"], w["c"]
+    tT = w["tT"] * nt_sample / w["NT"]
+    q = np.ascontiguousarray(w["q"][: nt_sample + 1])
+    t0 = time.perf_counter()
+    H = oracle.Hierarchy(N, nt_sample, w["L"], tT, k, c)
+    b = oracle.assemble_load(N, nt_sample, w["L"] / N, q)
+    u, st, cyc, hist = H.solve(b, tol=tol)
+    dt = time.perf_counter() - t0
+    dofs = (N + 1) * (nt_sample + 1)
+    return dict(value=dofs / dt, seconds=dt, dofs=dofs, cycles=cyc, status=st, relres=float(hist[-1]))
+
+
+def oracle_time_stepping(w):
+    """Exact sequential implicit time stepping (the oracle's direct solver) on the full grid."""
+    import oracle
+
+    N, NT = w["N"], w["NT"]
+    if w["k"] is None:
+        k, c = oracle.simp(w["chi"], w["simp"])
+    else:
+        k, c = w["k"], w["c"]
+    t0 = time.perf_counter()
+    b = oracle.assemble_load(N, NT, w["L"] / N, w["q"])
+    oracle.exact(N, NT, w["L"], w["tT"], k, c, b)
+    dt = time.perf_counter() - t0
+    return dict(value=(N + 1) * (NT + 1) / dt, seconds=dt)
+
+
+def cpu_baseline_obj(w, nt_sample=256):
+    s = oracle_sample(w, nt_sample)
+    ts = oracle_time_stepping(w)
+    return {"value": s["value"], "unit": "DOF/s", "cores": 1, "kind": "oracle",
+            "sample": "oracle STMG (FP64 C, Alg. 1 with the same options) solving the first %d of %d time steps "
+                      "of the workload (%d DOFs, same dx, dt, material and load) to %.0e: %d cycles in %.1f s"
+                      % (nt_sample, w["NT"], s["dofs"], TOL, s["cycles"], s["seconds"]),
+            "time_stepping": {"value": ts["value"], "unit": "DOF/s", "seconds": ts["seconds"],
+                              "what": "oracle exact sequential time stepping (Thomas per step) on the full grid"}}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = load_workload(args.workload)
+    nt_sample = 128
+    for _ in range(args.warmup):
+        oracle_sample(w, nt_sample)
+    vals, secs = [], []
+    for _ in range(args.steps):
+        s = oracle_sample(w, nt_sample)
+        vals.append(s["value"])
+        secs.append(s["seconds"])
+    tot = sum(secs)
+    dofs = (w["N"] + 1) * (nt_sample + 1)
+    value = dofs * args.steps / tot
+    sample = ("oracle STMG (FP64 C, one core) solving the first %d of %d time steps of %s to %.0e per step"
+              % (nt_sample, w["NT"], w["name"], TOL))
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "%s_timeslab%d" % (w["name"], nt_sample), "N": w["N"], "NT": nt_sample},
+        "cpu_baseline": {"value": value, "unit": "DOF/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "DOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import torch.distributed as dist
+
+    import paper_2505_10168_gb300 as pkg
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    w = load_workload(args.workload)
+    N, NT, L, tT = w["N"], w["NT"], w["L"], w["tT"]
+    dofs = (N + 1) * (NT + 1)
+    stream = torch.cuda.current_stream(dev)
+    if w["k"] is None:
+        chi = torch.tensor(w["chi"], device=dev)
+        k = torch.empty(N, dtype=torch.float64, device=dev)
+        c = torch.empty_like(k)
+        pkg.simp(chi, w["simp"], k, c)
+    else:
+        k = torch.tensor(w["k"], device=dev)
+        c = torch.tensor(w["c"], device=dev)
+    q = torch.tensor(w["q"], device=dev)
+    u = torch.empty((NT + 1, N + 1), dtype=torch.float64, device=dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    solver = pkg.Solver(N, NT, L, tT, k, c, precision=args.precision, tol=TOL)
+    setup_ms = 1e3 * (time.perf_counter() - t0)
+
+    for _ in range(args.warmup):
+        st, cyc, rr = solver.solve(u, q=q)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(gpu_smi_id(dev))
+    clk.start()
+    time.sleep(0.3)
+    l0 = pkg.kernel_launches()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    statuses = []
+    for _ in range(args.steps):
+        statuses.append(solver.solve(u, q=q))
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    launches = pkg.kernel_launches() - l0
+    clocks = clk.stop()
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / args.steps
+    value = world * dofs * args.steps / (ms * 1e-3)
+    cycles = statuses[-1][1]
+    relres = statuses[-1][2]
+    ok = all(s[0] == "ok" and s[2] < TOL for s in statuses)
+
+    # ---- dominant kernel: FP64 Jacobi sweep on the finest level, timed live ----
+    roofline = None
+    try:
+        b = torch.empty_like(u)
+        solver.assemble_load(q, b)
+        uu = torch.zeros_like(u)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        solver.smooth(0, uu, b, 0)
+        nsw = 20
+        e[0].record(stream)
+        solver.smooth(0, uu, b, 0)
+        e[1].record(stream)
+        e[2].record(stream)
+        solver.smooth(0, uu, b, nsw)
+        e[3].record(stream)
+        torch.cuda.synchronize()
+        sweep_ms = (e[2].elapsed_time(e[3]) - e[0].elapsed_time(e[1])) / nsw
+        flops = 15.0 * dofs  # 7 FMA + 1 subtraction per DOF
+        bytes_alg = 24.0 * dofs  # read u, b; write u (FP64)
+        ach = flops / (sweep_ms * 1e-3) / 1e12
+        roofline = {"kernel": "k_jacobi<double> (finest level)", "bound": "alu", "achieved": ach,
+                    "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s", "frac": ach / NOMINAL_FP64_TFLOPS,
+                    "traffic": None, "ms_per_launch": sweep_ms,
+                    "hbm_gbs": bytes_alg / (sweep_ms * 1e-3) / 1e9,
+                    "hbm_frac_of_measured": bytes_alg / (sweep_ms * 1e-3) / 1e9 /
+                    measured_peaks().get("hbm_gbs", 6788.3),
+                    "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (FP64 FMA throughput measured 1.20)"}
+        del b, uu
+    except Exception as ex:  # report, do not hide
+        roofline = {"error": repr(ex)}
+
+    # ---- end to end through the C ABI with host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        qh = torch.tensor(w["q"]).pin_memory()
+        uh = torch.empty((NT + 1, N + 1), dtype=torch.float64).pin_memory()
+        solver.solve(uh, q=qh)
+        barrier()
+        t1 = time.perf_counter()
+        ksteps = max(1, min(args.steps, 3))
+        for _ in range(ksteps):
+            solver.solve(uh, q=qh)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t1
+        if world > 1:
+            t = torch.tensor([el], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        e2e = {"value": world * dofs * ksteps / el, "unit": "DOF/s", "h2d_bytes_per_step": int(qh.numel() * 8),
+               "d2h_bytes_per_step": int(uh.numel() * 8 + 8 * (cycles + 2)), "steps": ksteps}
+        del qh, uh
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_obj(w)
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": w["name"], "N": N, "NT": NT, "dofs": dofs, "precision": args.precision,
+                       "tol": TOL, "levels": solver.num_levels, "path": solver.path(), "cycles": cycles,
+                       "relres": relres, "converged": ok, "setup_ms": setup_ms,
+                       "l2": "no flush: every vector (%d MB) exceeds the 129 MB L2" % (dofs * 8 // 2 ** 20),
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "clocks": clocks, "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

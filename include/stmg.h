@@ -1,0 +1,168 @@
+/*
+ * stmg.h -- C ABI of the GB300 space-time multigrid (STMG) library.
+ *
+ * The library solves the all-at-once backward-Euler / linear-finite-element system
+ * J u = b of the 1D transient heat equation
+ *     c dT/dt - d/dx (k dT/dx) = q  on [0, L] x [0, t_T],
+ *     T = 0 at t = 0,  T = 0 at x = 0,  dT/dx = 0 at x = L            (Sec. 2, Eq. of the PDE)
+ * with element-wise constant k, c, q (Sec. 2.2), and its adjoint J^T Lambda = rhs
+ * (Sec. 7.2), by the space-time multigrid V-cycle of Alg. 1: damped pointwise Jacobi
+ * (Sec. 3.1), x- or t-semi-coarsening chosen by the effective anisotropy parameter
+ * lambda_eff = sqrt(min D_e max D_e) dt / dx^2 (Sec. 4, Alg. 3; Alg. 4 with min_nel),
+ * rediscretised coarse operators with conductivity (K) or resistivity (R) averaging
+ * (Sec. 3.1, 5.1), causal prolongation with R = s P^T (Sec. 3.1), an exact coarsest
+ * solve, and the Dirichlet treatment J = B J_Neu B + W_Diri (I - B) (Appendix A).
+ *
+ * Grid and layout.  N = nel elements (dx = L/N), NT = nt time steps (dt = t_T/NT).
+ * A space-time vector (u, b, Lambda, rhs) is a dense row-major FP64 array of
+ * (NT+1) x (N+1) values: row n is time level t_n, column i is node x_i = i dx.
+ * Element arrays (k, c, chi, gradient) have N values; element loads q have
+ * (NT+1) x N values (row n = load at t_n; row 0 is ignored because b_0 = 0).
+ *
+ * Memory.  Unless stated otherwise every array argument may be device memory or host
+ * memory (pageable or pinned); host arrays are copied through the library's device
+ * buffers on the handle's stream.  The caller owns all argument arrays.  The handle
+ * owns the level hierarchy and all scratch, allocated at stmg_create and freed by
+ * stmg_destroy.
+ *
+ * Streams and synchronisation.  All device work of a handle is issued on the CUDA
+ * stream given to stmg_create (NULL = legacy default stream).  Every call returns only
+ * after its outputs are complete.  A handle must not be used by two host threads at
+ * once; distinct handles are independent.
+ *
+ * Errors.  Every call returns a stmg_status; no call exits or traps.  On an error the
+ * message is available from stmg_last_error(handle) (or stmg_last_error(NULL) when no
+ * handle exists).  A solve that stops on the divergence or cycle limit still returns
+ * its last iterate, cycle count and relative residual.
+ */
+#ifndef STMG_H
+#define STMG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct stmg_handle* stmg_t;
+
+typedef enum {
+    STMG_OK = 0,
+    STMG_EINVAL = 1,    /* invalid argument (sizes, non-positive k/c/L/t_T, NaN, bad options) */
+    STMG_ENOMEM = 2,    /* device or host allocation failed; the handle is unchanged */
+    STMG_ECUDA = 3,     /* a CUDA runtime call failed; see stmg_last_error */
+    STMG_EDIVERGED = 4, /* relative residual exceeded div_tol (Sec. 3.1 termination rule) */
+    STMG_EMAXITER = 5   /* max_cycles reached before tol (Sec. 3.1 termination rule) */
+} stmg_status;
+
+enum { STMG_INTERP_CAUSAL = 0 };                            /* Sec. 3.1 / 5.1 "C" */
+enum { STMG_REASM_K = 0, STMG_REASM_R = 1 };                /* Sec. 3.1 "K", Sec. 5.1 "R" */
+enum { STMG_FP64 = 0, STMG_MIXED = 1 };                     /* precision of the V-cycle */
+enum { STMG_COARSEST = 0, STMG_XCOARSEN = 1, STMG_TCOARSEN = 2 };
+
+/* Solver options; stmg_default_opts fills the defaults given in brackets. */
+typedef struct {
+    int nu;                    /* [5] pre- and post-smoothing steps of Alg. 1 (paper: 5, and 20 in Sec. 6-7) */
+    double omega;              /* [0.5] Jacobi damping (Sec. 3.1) */
+    double lambda_crit;        /* [0.25] t-coarsen iff lambda_eff < lambda_crit (Alg. 3; Sec. 5.2 value) */
+    int interp;                /* [STMG_INTERP_CAUSAL] prolongation */
+    int reassembly;            /* [STMG_REASM_R] coarse-level material averaging */
+    int min_nel;               /* [0] M of Alg. 4 (t-coarsen when N/2 < M); 0 = Alg. 3 */
+    int num_levels;            /* [0] > 0: exactly this many levels N_l */
+    int max_levels;            /* [30] cap on N_l when num_levels == 0 */
+    long long max_coarse_dofs; /* [512] num_levels == 0: stop at the first level with <= this many DOFs */
+    double deff_fixed;         /* [0] > 0: design-independent D_eff on every level (Sec. 7.2) */
+    int precision;             /* [STMG_FP64] STMG_FP64: FP64 V-cycles (Alg. 1 as written).
+                                  STMG_MIXED: FP64 defect correction around FP32 V-cycles; the fine
+                                  residual, the coarse material and the coarsest solve stay FP64. */
+    double tol;                /* [1e-10] stop when ||J u - b|| / ||b|| < tol (Sec. 3.1) */
+    double div_tol;            /* [1e9] stop (diverged) when the relative residual exceeds this */
+    int max_cycles;            /* [100] cycle limit (Sec. 3.1) */
+} stmg_opts;
+
+void stmg_default_opts(stmg_opts* opts);
+
+/* Build the level hierarchy for N = nel elements and NT = nt steps on [0, L] x [0, t_end]
+ * with element conductivity k_el[nel] > 0 and heat capacity c_el[nel] > 0 (host or
+ * device).  Runs the coarsening strategy (Alg. 3/4), averages the coarse materials
+ * (Sec. 3.1/5.1), computes W_Diri per level (Appendix A) and allocates every level's
+ * vectors.  opts NULL = defaults.  stream: a cudaStream_t or NULL. */
+stmg_status stmg_create(stmg_t* handle, int nel, int nt, double L, double t_end, const double* k_el,
+                        const double* c_el, const stmg_opts* opts, void* stream);
+
+/* Replace k and c (same nel); re-runs the planner.  With deff_fixed > 0 the coarsening
+ * path, and so every level size, is unchanged (Sec. 7.2); otherwise levels may be
+ * re-allocated. */
+stmg_status stmg_update_material(stmg_t handle, const double* k_el, const double* c_el);
+
+void stmg_destroy(stmg_t handle);
+const char* stmg_last_error(stmg_t handle);
+
+/* SIMP material model (Sec. 2.1): k = k_ins + (k_con - k_ins) chi^p_k and
+ * c = c_ins + (c_con - c_ins) chi^p_c with simp6 = {k_ins, k_con, c_ins, c_con, p_k, p_c}
+ * (host array).  chi, k_el, c_el: nel values, all device memory.  stream may be NULL. */
+stmg_status stmg_simp(int nel, const double* chi, const double* simp6, double* k_el, double* c_el, void* stream);
+
+/* Nodal load b = B b_Neu from element loads q_el[(nt+1) x nel] (Sec. 2.2, Appendix A):
+ * b[n][i] = dx/2 (q[n][i-1] + q[n][i]) for n >= 1, i >= 1 (q[n][N] taken as 0); 0 on
+ * the Dirichlet DOFs.  b: (nt+1) x (nel+1). */
+stmg_status stmg_assemble_load(stmg_t handle, const double* q_el, double* b);
+
+/* Solve J u = b (Sec. 2.2) by V-cycles (Alg. 1) until the Sec. 3.1 termination rule.
+ * Exactly one of q_el (element loads, assembled as in stmg_assemble_load) and b_nodal
+ * ((nt+1) x (nel+1)) is non-NULL.  u: (nt+1) x (nel+1) output; with warm != 0 its
+ * content is the initial guess (warm restart, Sec. 7.2), else the guess is 0.
+ * cycles / relres (may be NULL) receive the cycle count and ||J u - b|| / ||b||.
+ * Returns STMG_OK, STMG_EDIVERGED or STMG_EMAXITER (u filled in all three cases). */
+stmg_status stmg_solve(stmg_t handle, const double* q_el, const double* b_nodal, double* u, int warm, int* cycles,
+                       double* relres);
+
+/* Solve the adjoint system J^T lam = rhs (Sec. 7.2) with the same hierarchy, the
+ * transposed level operators and the unchanged causal prolongation.  For the
+ * compliance objective rhs = b dt / Theta_ref.  Shapes and results as stmg_solve. */
+stmg_status stmg_solve_adjoint(stmg_t handle, const double* rhs, double* lam, int warm, int* cycles,
+                               double* relres);
+
+/* Design sensitivity of Theta = b^T u dt / Theta_ref (Sec. 7.1) by the discrete adjoint
+ * method (Sec. 7.2): dtheta_dchi[e] = -Lambda^T (dJ/dchi_e) u with
+ * dJ/dchi_e = k'(chi_e) dJ/dk_e + c'(chi_e) dJ/dc_e from the SIMP model (Sec. 2.1).
+ * u solves J u = b and lam solves J^T lam = b dt / Theta_ref.  chi: nel values;
+ * simp6: host array as in stmg_simp; dtheta_dchi: nel outputs. */
+stmg_status stmg_sensitivity(stmg_t handle, const double* chi, const double* simp6, const double* u,
+                             const double* lam, double* dtheta_dchi);
+
+/* Theta = b^T u dt / theta_ref (Sec. 7.1); theta: host output. */
+stmg_status stmg_objective(stmg_t handle, const double* b, const double* u, double theta_ref, double* theta);
+
+/* ---- hierarchy inspection ------------------------------------------------------------ */
+int stmg_num_levels(stmg_t handle);
+/* Level l (0 = finest): sizes, how level l+1 is built (STMG_XCOARSEN / STMG_TCOARSEN, or
+ * STMG_COARSEST on the last level), mesh widths, W_Diri and lambda_eff.  Any output
+ * pointer may be NULL. */
+stmg_status stmg_level_info(stmg_t handle, int level, int* nel, int* nt, int* next, double* dx, double* dt,
+                            double* w_diri, double* lambda_eff);
+/* Coarse-level material of level l into host arrays k[nel_l], c[nel_l]. */
+stmg_status stmg_level_material(stmg_t handle, int level, double* k, double* c);
+
+/* ---- building blocks on one level (space-time vectors of level l's shape) ------------- */
+/* y = J_l u (adjoint != 0: y = J_l^T u). */
+stmg_status stmg_apply(stmg_t handle, int level, int adjoint, const double* u, double* y);
+/* nsweeps damped-Jacobi steps u <- u + omega D^-1 (b - J_l u) in place (Sec. 3.1). */
+stmg_status stmg_smooth(stmg_t handle, int level, int adjoint, int nsweeps, double* u, const double* b);
+/* bc = R_l r = s P_l^T r (level l -> l+1, Sec. 3.1). */
+stmg_status stmg_restrict(stmg_t handle, int level, const double* r, double* bc);
+/* u += P_l z (level l+1 -> l, Sec. 3.1). */
+stmg_status stmg_prolong_add(stmg_t handle, int level, const double* z, double* u);
+/* Exact solve of J_l u = b (adjoint: J_l^T u = b) by implicit time stepping with one
+ * tridiagonal solve per step; the coarsest-level solver of Alg. 1. */
+stmg_status stmg_exact_solve(stmg_t handle, int level, int adjoint, const double* b, double* u);
+/* One V-cycle of Alg. 1 on the finest level, u updated in place, in the precision of
+ * the options (STMG_MIXED: one FP64 defect-correction step around one FP32 cycle). */
+stmg_status stmg_vcycle(stmg_t handle, int adjoint, double* u, const double* b);
+
+/* ---- statistics ------------------------------------------------------------------------ */
+/* Number of CUDA kernels this library has launched in this process so far (all handles). */
+unsigned long long stmg_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* STMG_H */

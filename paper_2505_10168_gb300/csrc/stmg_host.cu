@@ -1,0 +1,793 @@
+// stmg_host.cu -- host side of the STMG library: the C ABI of include/stmg.h, the
+// coarsening planner (Alg. 3/4), the level hierarchy in device memory, and the
+// V-cycle / solver loops that enqueue the kernels of stmg_kernels.cu on the handle's
+// stream.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "stmg.h"
+#include "stmg_internal.h"
+
+using namespace stmg;
+
+namespace {
+
+thread_local std::string g_global_error;
+
+// One level of the hierarchy.
+struct Level {
+  int N = 0, NT = 0, pitch = 0, next = STMG_COARSEST;
+  double dx = 0, dt = 0, W = 0, lam = 0;
+  std::vector<double> k, c;  // host copies of the level material
+  size_t nvec = 0;           // (NT+1) * pitch
+  // device
+  double* dk = nullptr;      // k, c (N values each)
+  double* dc = nullptr;
+  double* cf64 = nullptr;    // kNumCoef * pitch
+  float* cf32 = nullptr;
+  double* th = nullptr;      // Thomas factors: 6 arrays of N+2 doubles
+  double *u = nullptr, *b = nullptr, *t = nullptr;    // FP64 vectors
+  float *u32 = nullptr, *b32 = nullptr, *t32 = nullptr;  // FP32 vectors (mixed precision)
+};
+
+}  // namespace
+
+struct stmg_handle {
+  stmg_opts o{};
+  cudaStream_t s = nullptr;
+  int N = 0, NT = 0;
+  double L = 0, tT = 0;
+  std::vector<Level> lev;
+  double* partials = nullptr;  // kNormBlocks
+  double* scal = nullptr;      // device scalars
+  double* hscal = nullptr;     // pinned host scalars
+  double* qstage = nullptr;    // device staging for host element loads
+  size_t qstage_n = 0;
+  double* sens = nullptr;      // sensitivity scratch
+  size_t sens_n = 0;
+  double* gstage = nullptr;    // element-array staging (chi, gradient)
+  std::string err;
+};
+
+namespace {
+
+stmg_status fail(stmg_t h, stmg_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (h) h->err = buf;
+  else g_global_error = buf;
+  return st;
+}
+
+#define CK(call)                                                                                 \
+  do {                                                                                           \
+    cudaError_t e_ = (call);                                                                     \
+    if (e_ != cudaSuccess) {                                                                     \
+      return fail(h, e_ == cudaErrorMemoryAllocation ? STMG_ENOMEM : STMG_ECUDA, "%s: %s (%s:%d)", #call, \
+                  cudaGetErrorString(e_), __FILE__, __LINE__);                                   \
+    }                                                                                            \
+  } while (0)
+
+#define CKS(expr)                         \
+  do {                                    \
+    stmg_status st_ = (expr);             \
+    if (st_ != STMG_OK) return st_;       \
+  } while (0)
+
+template <typename T>
+stmg_status dalloc(stmg_t h, T** p, size_t n) {
+  *p = nullptr;
+  if (n == 0) n = 1;
+  cudaError_t e = cudaMalloc((void**)p, n * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return fail(h, STMG_ENOMEM, "cudaMalloc of %zu bytes failed: %s", n * sizeof(T), cudaGetErrorString(e));
+  }
+  return STMG_OK;
+}
+
+template <typename T>
+void dfree(T*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+void free_level(Level& L) {
+  dfree(L.dk); dfree(L.dc); dfree(L.cf64); dfree(L.cf32); dfree(L.th);
+  dfree(L.u); dfree(L.b); dfree(L.t); dfree(L.u32); dfree(L.b32); dfree(L.t32);
+}
+
+bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+// --------------------------------------------------------------------------------------
+// Planner: Alg. 3 (Alg. 4 with min_nel).  lambda_eff = D_eff dt / dx^2 with
+// D_eff = sqrt(min_e k_e/c_e * max_e k_e/c_e) or the fixed design-independent D_eff of
+// Sec. 7.2.  x-coarsening averages resistivity (R) or conductivity (K) and heat capacity
+// over element pairs; t-coarsening keeps the material and doubles dt.
+// --------------------------------------------------------------------------------------
+double level_lambda(const stmg_opts& o, const Level& L) {
+  double deff = o.deff_fixed;
+  if (!(deff > 0.0)) {
+    double lo = L.k[0] / L.c[0], hi = lo;
+    for (int e = 1; e < L.N; ++e) {
+      const double d = L.k[e] / L.c[e];
+      lo = std::min(lo, d);
+      hi = std::max(hi, d);
+    }
+    deff = std::sqrt(lo * hi);
+  }
+  return deff * L.dt / (L.dx * L.dx);
+}
+
+double level_wdiri(const Level& L) {
+  const double cmax = *std::max_element(L.c.begin(), L.c.end());
+  const double kmax = *std::max_element(L.k.begin(), L.k.end());
+  return cmax * L.dx / L.dt + kmax / L.dx;
+}
+
+std::vector<Level> plan_levels(const stmg_opts& o, int N, int NT, double Ldom, double tT, const double* k,
+                               const double* c) {
+  std::vector<Level> out;
+  Level f;
+  f.N = N; f.NT = NT; f.dx = Ldom / N; f.dt = tT / NT;
+  f.k.assign(k, k + N);
+  f.c.assign(c, c + N);
+  out.push_back(std::move(f));
+  const int cap = o.num_levels > 0 ? o.num_levels : std::max(1, o.max_levels);
+  while (true) {
+    Level& L = out.back();
+    L.W = level_wdiri(L);
+    L.lam = level_lambda(o, L);
+    L.next = STMG_COARSEST;
+    if ((int)out.size() >= cap) break;
+    const long long dofs = (long long)(L.NT + 1) * (L.N + 1);
+    if (o.num_levels <= 0 && dofs <= o.max_coarse_dofs) break;
+    const bool can_x = L.N % 2 == 0 && L.N >= 2;
+    const bool can_t = L.NT % 2 == 0 && L.NT >= 2;
+    const bool want_t = L.lam < o.lambda_crit || (o.min_nel > 0 && L.N / 2 < o.min_nel);
+    int type;
+    if (want_t) type = can_t ? STMG_TCOARSEN : (can_x ? STMG_XCOARSEN : STMG_COARSEST);
+    else type = can_x ? STMG_XCOARSEN : (can_t ? STMG_TCOARSEN : STMG_COARSEST);
+    if (type == STMG_COARSEST) break;
+    L.next = type;
+    Level C;
+    if (type == STMG_XCOARSEN) {
+      C.N = L.N / 2; C.NT = L.NT; C.dx = 2.0 * L.dx; C.dt = L.dt;
+      C.k.resize(C.N);
+      C.c.resize(C.N);
+      for (int e = 0; e < C.N; ++e) {
+        const double ka = L.k[2 * e], kb = L.k[2 * e + 1];
+        if (o.reassembly == STMG_REASM_R) {
+          const double rho = (1.0 / ka + 1.0 / kb) / 2.0;  // mean thermal resistivity
+          C.k[e] = 1.0 / rho;
+        } else {
+          C.k[e] = (ka + kb) / 2.0;
+        }
+        C.c[e] = (L.c[2 * e] + L.c[2 * e + 1]) / 2.0;
+      }
+    } else {
+      C.N = L.N; C.NT = L.NT / 2; C.dx = L.dx; C.dt = 2.0 * L.dt;
+      C.k = L.k;
+      C.c = L.c;
+    }
+    out.push_back(std::move(C));
+  }
+  for (Level& L : out) {
+    L.pitch = level_pitch(L.N);
+    L.nvec = (size_t)(L.NT + 1) * L.pitch;
+  }
+  return out;
+}
+
+// Thomas factors of (M/dt + K) restricted to nodes 1..N, from the host material.
+void thomas_factors(const Level& L, std::vector<double>& out) {
+  const int N = L.N;
+  const size_t S = N + 2;
+  out.assign(6 * S, 0.0);
+  double* lo = &out[0];
+  double* inv = &out[S];
+  double* cp = &out[2 * S];
+  double* pl = &out[3 * S];
+  double* pc = &out[4 * S];
+  double* pr = &out[5 * S];
+  std::vector<double> up(S, 0.0), di(S, 0.0);
+  for (int i = 1; i <= N; ++i) {
+    const double ml = L.c[i - 1] * L.dx / (6.0 * L.dt), sl = L.k[i - 1] / L.dx;
+    const double mr = i < N ? L.c[i] * L.dx / (6.0 * L.dt) : 0.0, sr = i < N ? L.k[i] / L.dx : 0.0;
+    lo[i] = i >= 2 ? ml - sl : 0.0;
+    up[i] = i < N ? mr - sr : 0.0;
+    di[i] = 2.0 * ml + sl + 2.0 * mr + sr;
+    pl[i] = i >= 2 ? -ml : 0.0;
+    pc[i] = -2.0 * (ml + mr);
+    pr[i] = i < N ? -mr : 0.0;
+  }
+  double cprev = 0.0;
+  for (int i = 1; i <= N; ++i) {
+    const double den = di[i] - lo[i] * cprev;
+    inv[i] = 1.0 / den;
+    cp[i] = up[i] * inv[i];
+    cprev = cp[i];
+  }
+}
+
+// Device set-up of one level (material, coefficients, Thomas factors); vectors are
+// allocated by alloc_vectors.
+stmg_status setup_level(stmg_t h, Level& L) {
+  if (!L.dk) CKS(dalloc(h, &L.dk, L.N));
+  if (!L.dc) CKS(dalloc(h, &L.dc, L.N));
+  if (!L.cf64) CKS(dalloc(h, &L.cf64, (size_t)kNumCoef * L.pitch));
+  if (!L.cf32) CKS(dalloc(h, &L.cf32, (size_t)kNumCoef * L.pitch));
+  if (!L.th) CKS(dalloc(h, &L.th, 6 * (size_t)(L.N + 2)));
+  CK(cudaMemcpyAsync(L.dk, L.k.data(), L.N * sizeof(double), cudaMemcpyHostToDevice, h->s));
+  CK(cudaMemcpyAsync(L.dc, L.c.data(), L.N * sizeof(double), cudaMemcpyHostToDevice, h->s));
+  CK(launch_build_coef(L.N, L.pitch, L.dx, L.dt, L.W, h->o.omega, L.dk, L.dc, L.cf64, L.cf32, h->s));
+  std::vector<double> th;
+  thomas_factors(L, th);
+  CK(cudaMemcpyAsync(L.th, th.data(), th.size() * sizeof(double), cudaMemcpyHostToDevice, h->s));
+  // the host vector must outlive the async copy
+  CK(cudaStreamSynchronize(h->s));
+  return STMG_OK;
+}
+
+template <typename T>
+stmg_status zero_alloc(stmg_t h, T** p, size_t n) {
+  CKS(dalloc(h, p, n));
+  CK(cudaMemsetAsync(*p, 0, n * sizeof(T), h->s));
+  return STMG_OK;
+}
+
+stmg_status ensure_fp64(stmg_t h, Level& L) {
+  if (!L.u) CKS(zero_alloc(h, &L.u, L.nvec));
+  if (!L.b) CKS(zero_alloc(h, &L.b, L.nvec));
+  if (!L.t) CKS(zero_alloc(h, &L.t, L.nvec));
+  return STMG_OK;
+}
+
+stmg_status ensure_fp32(stmg_t h, Level& L) {
+  if (!L.u32) CKS(zero_alloc(h, &L.u32, L.nvec));
+  if (!L.b32) CKS(zero_alloc(h, &L.b32, L.nvec));
+  if (!L.t32) CKS(zero_alloc(h, &L.t32, L.nvec));
+  return STMG_OK;
+}
+
+stmg_status alloc_vectors(stmg_t h) {
+  for (size_t l = 0; l < h->lev.size(); ++l) {
+    Level& L = h->lev[l];
+    if (l == 0 || h->o.precision == STMG_FP64) CKS(ensure_fp64(h, L));
+    if (h->o.precision == STMG_MIXED) CKS(ensure_fp32(h, L));
+  }
+  return STMG_OK;
+}
+
+template <typename T>
+LevelView<T> view(const Level& L, double omega);
+template <>
+LevelView<double> view<double>(const Level& L, double omega) {
+  return LevelView<double>{L.N, L.NT, L.pitch, L.cf64, L.W, omega / L.W};
+}
+template <>
+LevelView<float> view<float>(const Level& L, double omega) {
+  return LevelView<float>{L.N, L.NT, L.pitch, L.cf32, (float)L.W, (float)(omega / L.W)};
+}
+
+ThomasView thomas_view(const Level& L) {
+  const size_t S = L.N + 2;
+  return ThomasView{L.N, L.NT, L.pitch, L.th, L.th + S, L.th + 2 * S, L.th + 3 * S, L.th + 4 * S, L.th + 5 * S, L.W};
+}
+
+// Level vectors for precision T.
+template <typename T>
+struct Vecs {
+  T *u, *b, *t;
+};
+template <typename T>
+Vecs<T> vecs(Level& L);
+template <>
+Vecs<double> vecs<double>(Level& L) { return {L.u, L.b, L.t}; }
+template <>
+Vecs<float> vecs<float>(Level& L) { return {L.u32, L.b32, L.t32}; }
+template <typename T>
+void set_u(Level& L, T* u);
+template <>
+void set_u<double>(Level& L, double* u) { L.u = u; }
+template <>
+void set_u<float>(Level& L, float* u) { L.u32 = u; }
+template <typename T>
+void set_t(Level& L, T* t);
+template <>
+void set_t<double>(Level& L, double* t) { L.t = t; }
+template <>
+void set_t<float>(Level& L, float* t) { L.t32 = t; }
+
+// nsweeps Jacobi steps on level L ping-ponging u and t (the level's u pointer follows
+// the current iterate).
+template <typename T>
+stmg_status smooth_level(stmg_t h, Level& L, bool adj, int nsweeps) {
+  const LevelView<T> lv = view<T>(L, h->o.omega);
+  for (int s = 0; s < nsweeps; ++s) {
+    Vecs<T> v = vecs<T>(L);
+    CK(launch_jacobi<T>(lv, adj, v.u, v.b, v.t, h->s));
+    set_u<T>(L, v.t);
+    set_t<T>(L, v.u);
+  }
+  return STMG_OK;
+}
+
+// Alg. 1, VCycle(l, u, b), in precision T on the level's own u and b.
+template <typename T>
+stmg_status vcycle(stmg_t h, int l, bool adj) {
+  Level& L = h->lev[l];
+  if (l == (int)h->lev.size() - 1) {
+    Vecs<T> v = vecs<T>(L);
+    CK(launch_exact<T>(thomas_view(L), adj, v.b, v.u, h->s));
+    return STMG_OK;
+  }
+  Level& C = h->lev[l + 1];
+  CKS(smooth_level<T>(h, L, adj, h->o.nu));
+  {
+    Vecs<T> v = vecs<T>(L);
+    Vecs<T> vc = vecs<T>(C);
+    CK(launch_residual<T>(view<T>(L, h->o.omega), adj, v.u, v.b, v.t, h->s));
+    CK(launch_restrict<T>(L.next, L.N, L.NT, L.pitch, v.t, C.N, C.NT, C.pitch, vc.b, h->s));
+    CK(cudaMemsetAsync(vc.u, 0, C.nvec * sizeof(T), h->s));
+  }
+  CKS(vcycle<T>(h, l + 1, adj));
+  {
+    Vecs<T> v = vecs<T>(L);
+    Vecs<T> vc = vecs<T>(C);
+    CK(launch_prolong_add<T>(L.next, L.N, L.NT, L.pitch, v.u, C.N, C.NT, C.pitch, vc.u, h->s));
+  }
+  CKS(smooth_level<T>(h, L, adj, h->o.nu));
+  return STMG_OK;
+}
+
+// Read one device double (after the stream's pending work).
+stmg_status read_scalar(stmg_t h, const double* d, double* out) {
+  CK(cudaMemcpyAsync(h->hscal, d, sizeof(double), cudaMemcpyDeviceToHost, h->s));
+  CK(cudaStreamSynchronize(h->s));
+  *out = h->hscal[0];
+  return STMG_OK;
+}
+
+// Copy a dense (rows x cols) user array into a padded level buffer (or back).
+stmg_status copy_in(stmg_t h, double* dst, int pitch, const double* src, int rows, int cols) {
+  CK(cudaMemcpy2DAsync(dst, (size_t)pitch * sizeof(double), src, (size_t)cols * sizeof(double),
+                       (size_t)cols * sizeof(double), rows, cudaMemcpyDefault, h->s));
+  return STMG_OK;
+}
+stmg_status copy_out(stmg_t h, double* dst, const double* src, int pitch, int rows, int cols) {
+  CK(cudaMemcpy2DAsync(dst, (size_t)cols * sizeof(double), src, (size_t)pitch * sizeof(double),
+                       (size_t)cols * sizeof(double), rows, cudaMemcpyDefault, h->s));
+  return STMG_OK;
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Element loads -> nodal b on level 0.
+stmg_status assemble_into(stmg_t h, const double* q, double* b) {
+  Level& L = h->lev[0];
+  const double* qd = q;
+  if (!is_device_ptr(q)) {
+    const size_t n = (size_t)(L.NT + 1) * L.N;
+    if (h->qstage_n < n) {
+      dfree(h->qstage);
+      h->qstage_n = 0;
+      CKS(dalloc(h, &h->qstage, n));
+      h->qstage_n = n;
+    }
+    CK(cudaMemcpyAsync(h->qstage, q, n * sizeof(double), cudaMemcpyDefault, h->s));
+    qd = h->qstage;
+  }
+  CK(launch_assemble_load(L.N, L.NT, L.pitch, L.dx, qd, b, h->s));
+  return STMG_OK;
+}
+
+// ||b - J u||^2 on level 0 in FP64 (u null: ||b||^2).
+stmg_status resnorm2(stmg_t h, bool adj, const double* u, const double* b, double* out) {
+  Level& L = h->lev[0];
+  CK((launch_resnorm<double, double>(view<double>(L, h->o.omega), adj, u, b, nullptr, h->partials, h->scal,
+                                     h->s)));
+  return read_scalar(h, h->scal, out);
+}
+
+// The solver loop of Sec. 3.1 on level 0's u and b (already in place).
+stmg_status solve_loop(stmg_t h, bool adj, bool warm, int* cycles_out, double* relres_out) {
+  Level& L = h->lev[0];
+  const stmg_opts& o = h->o;
+  if (!warm) CK(cudaMemsetAsync(L.u, 0, L.nvec * sizeof(double), h->s));
+  double nb2 = 0.0;
+  CKS(resnorm2(h, adj, nullptr, L.b, &nb2));
+  int cycles = 0;
+  double rel = 0.0;
+  stmg_status st = STMG_EMAXITER;
+  if (nb2 == 0.0) {
+    CK(cudaMemsetAsync(L.u, 0, L.nvec * sizeof(double), h->s));
+    st = STMG_OK;
+  } else if (!std::isfinite(nb2)) {
+    return fail(h, STMG_EINVAL, "right-hand side contains NaN or Inf");
+  } else {
+    const double nb = std::sqrt(nb2);
+    double r2 = nb2;
+    if (o.precision == STMG_MIXED) {
+      CK(launch_defect(view<double>(L, o.omega), adj, L.u, L.b, L.b32, h->partials, h->scal, h->s));
+      CKS(read_scalar(h, h->scal, &r2));
+    } else if (warm) {
+      CKS(resnorm2(h, adj, L.u, L.b, &r2));
+    }
+    rel = std::sqrt(r2) / nb;
+    if (rel < o.tol) st = STMG_OK;
+    for (int cyc = 1; cyc <= o.max_cycles && st != STMG_OK; ++cyc) {
+      if (o.precision == STMG_MIXED) {
+        CK(cudaMemsetAsync(L.u32, 0, L.nvec * sizeof(float), h->s));
+        CKS(vcycle<float>(h, 0, adj));
+        CK(launch_add_correction(L.nvec, L.u, L.u32, h->s));
+        CK(launch_defect(view<double>(L, o.omega), adj, L.u, L.b, L.b32, h->partials, h->scal, h->s));
+        CKS(read_scalar(h, h->scal, &r2));
+      } else {
+        CKS(vcycle<double>(h, 0, adj));
+        CKS(resnorm2(h, adj, L.u, L.b, &r2));
+      }
+      rel = std::sqrt(r2) / nb;
+      cycles = cyc;
+      if (!(rel <= o.div_tol)) {  // also catches NaN
+        st = STMG_EDIVERGED;
+        break;
+      }
+      if (rel < o.tol) st = STMG_OK;
+    }
+  }
+  if (cycles_out) *cycles_out = cycles;
+  if (relres_out) *relres_out = rel;
+  return st;
+}
+
+stmg_status check_opts(stmg_t h, const stmg_opts& o) {
+  if (o.nu < 0 || !(o.omega > 0) || !std::isfinite(o.lambda_crit) || o.interp != STMG_INTERP_CAUSAL ||
+      (o.reassembly != STMG_REASM_K && o.reassembly != STMG_REASM_R) || o.min_nel < 0 || o.num_levels < 0 ||
+      o.num_levels > 60 || o.max_levels < 1 || o.max_levels > 60 || o.max_coarse_dofs < 1 ||
+      (o.precision != STMG_FP64 && o.precision != STMG_MIXED) || !(o.tol >= 0) || !(o.div_tol > 0) ||
+      o.max_cycles < 0 || !(o.deff_fixed >= 0))
+    return fail(h, STMG_EINVAL, "invalid stmg_opts");
+  return STMG_OK;
+}
+
+stmg_status read_material(stmg_t h, int n, const double* k, const double* c, std::vector<double>& hk,
+                          std::vector<double>& hc) {
+  if (!k || !c) return fail(h, STMG_EINVAL, "k_el and c_el must be non-NULL");
+  hk.resize(n);
+  hc.resize(n);
+  cudaStream_t s = h ? h->s : nullptr;
+  cudaError_t e1 = cudaMemcpyAsync(hk.data(), k, n * sizeof(double), cudaMemcpyDefault, s);
+  cudaError_t e2 = cudaMemcpyAsync(hc.data(), c, n * sizeof(double), cudaMemcpyDefault, s);
+  cudaError_t e3 = cudaStreamSynchronize(s);
+  if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess)
+    return fail(h, STMG_ECUDA, "reading k/c failed: %s", cudaGetErrorString(cudaGetLastError()));
+  for (int e = 0; e < n; ++e)
+    if (!finite_pos(hk[e]) || !finite_pos(hc[e]))
+      return fail(h, STMG_EINVAL, "k and c must be finite and > 0 (element %d: k=%g c=%g)", e, hk[e], hc[e]);
+  return STMG_OK;
+}
+
+stmg_status build_hierarchy(stmg_t h, const std::vector<double>& hk, const std::vector<double>& hc) {
+  std::vector<Level> nl = plan_levels(h->o, h->N, h->NT, h->L, h->tT, hk.data(), hc.data());
+  // keep device buffers of levels whose shape is unchanged
+  for (size_t l = 0; l < nl.size(); ++l) {
+    if (l < h->lev.size() && h->lev[l].N == nl[l].N && h->lev[l].NT == nl[l].NT) {
+      Level& old = h->lev[l];
+      std::swap(nl[l].dk, old.dk); std::swap(nl[l].dc, old.dc); std::swap(nl[l].cf64, old.cf64);
+      std::swap(nl[l].cf32, old.cf32); std::swap(nl[l].th, old.th); std::swap(nl[l].u, old.u);
+      std::swap(nl[l].b, old.b); std::swap(nl[l].t, old.t); std::swap(nl[l].u32, old.u32);
+      std::swap(nl[l].b32, old.b32); std::swap(nl[l].t32, old.t32);
+    }
+  }
+  for (Level& old : h->lev) free_level(old);
+  h->lev = std::move(nl);
+  for (Level& L : h->lev) CKS(setup_level(h, L));
+  CKS(alloc_vectors(h));
+  CK(cudaStreamSynchronize(h->s));
+  return STMG_OK;
+}
+
+stmg_status check_level(stmg_t h, int level) {
+  if (!h) return fail(nullptr, STMG_EINVAL, "NULL handle");
+  if (level < 0 || level >= (int)h->lev.size()) return fail(h, STMG_EINVAL, "level %d out of range", level);
+  return STMG_OK;
+}
+
+}  // namespace
+
+// ======================================================================================
+// C ABI
+// ======================================================================================
+extern "C" {
+
+void stmg_default_opts(stmg_opts* o) {
+  if (!o) return;
+  o->nu = 5;
+  o->omega = 0.5;
+  o->lambda_crit = 0.25;
+  o->interp = STMG_INTERP_CAUSAL;
+  o->reassembly = STMG_REASM_R;
+  o->min_nel = 0;
+  o->num_levels = 0;
+  o->max_levels = 30;
+  o->max_coarse_dofs = 512;
+  o->deff_fixed = 0.0;
+  o->precision = STMG_FP64;
+  o->tol = 1e-10;
+  o->div_tol = 1e9;
+  o->max_cycles = 100;
+}
+
+const char* stmg_last_error(stmg_t h) { return h ? h->err.c_str() : g_global_error.c_str(); }
+
+stmg_status stmg_create(stmg_t* out, int nel, int nt, double L, double t_end, const double* k_el,
+                        const double* c_el, const stmg_opts* opts, void* stream) {
+  stmg_t h = nullptr;
+  if (!out) return fail(nullptr, STMG_EINVAL, "NULL output handle pointer");
+  *out = nullptr;
+  if (nel < 1 || nt < 1 || !finite_pos(L) || !finite_pos(t_end))
+    return fail(nullptr, STMG_EINVAL, "need nel >= 1, nt >= 1, L > 0, t_end > 0");
+  h = new (std::nothrow) stmg_handle();
+  if (!h) return fail(nullptr, STMG_ENOMEM, "host allocation failed");
+  if (opts) h->o = *opts;
+  else stmg_default_opts(&h->o);
+  h->s = (cudaStream_t)stream;
+  h->N = nel; h->NT = nt; h->L = L; h->tT = t_end;
+  std::vector<double> hk, hc;
+  stmg_status st = check_opts(h, h->o);
+  if (st == STMG_OK) st = read_material(h, nel, k_el, c_el, hk, hc);
+  if (st == STMG_OK) st = dalloc(h, &h->partials, kNormBlocks);
+  if (st == STMG_OK) st = dalloc(h, &h->scal, 8);
+  if (st == STMG_OK) {
+    cudaError_t e = cudaMallocHost((void**)&h->hscal, 8 * sizeof(double));
+    if (e != cudaSuccess) st = fail(h, STMG_ENOMEM, "cudaMallocHost failed: %s", cudaGetErrorString(e));
+  }
+  if (st == STMG_OK) st = build_hierarchy(h, hk, hc);
+  if (st != STMG_OK) {
+    g_global_error = h->err;
+    stmg_destroy(h);
+    return st;
+  }
+  *out = h;
+  return STMG_OK;
+}
+
+void stmg_destroy(stmg_t h) {
+  if (!h) return;
+  if (h->s) cudaStreamSynchronize(h->s);
+  else cudaDeviceSynchronize();
+  for (Level& L : h->lev) free_level(L);
+  dfree(h->partials);
+  dfree(h->scal);
+  dfree(h->qstage);
+  dfree(h->sens);
+  dfree(h->gstage);
+  if (h->hscal) cudaFreeHost(h->hscal);
+  delete h;
+}
+
+stmg_status stmg_update_material(stmg_t h, const double* k_el, const double* c_el) {
+  if (!h) return fail(nullptr, STMG_EINVAL, "NULL handle");
+  std::vector<double> hk, hc;
+  CKS(read_material(h, h->N, k_el, c_el, hk, hc));
+  return build_hierarchy(h, hk, hc);
+}
+
+stmg_status stmg_simp(int nel, const double* chi, const double* simp6, double* k_el, double* c_el, void* stream) {
+  stmg_t h = nullptr;
+  if (nel < 1 || !chi || !simp6 || !k_el || !c_el) return fail(nullptr, STMG_EINVAL, "bad stmg_simp arguments");
+  Simp6 sp;
+  for (int i = 0; i < 6; ++i) sp.v[i] = simp6[i];
+  CK(launch_simp(nel, chi, sp, k_el, c_el, (cudaStream_t)stream));
+  CK(cudaStreamSynchronize((cudaStream_t)stream));
+  return STMG_OK;
+}
+
+stmg_status stmg_assemble_load(stmg_t h, const double* q_el, double* b) {
+  if (!h) return fail(nullptr, STMG_EINVAL, "NULL handle");
+  if (!q_el || !b) return fail(h, STMG_EINVAL, "NULL array");
+  Level& L = h->lev[0];
+  CKS(assemble_into(h, q_el, L.t));
+  CKS(copy_out(h, b, L.t, L.pitch, L.NT + 1, L.N + 1));
+  CK(cudaStreamSynchronize(h->s));
+  return STMG_OK;
+}
+
+static stmg_status solve_common(stmg_t h, bool adj, const double* q_el, const double* b_nodal, double* u, int warm,
+                                int* cycles, double* relres) {
+  if (!h) return fail(nullptr, STMG_EINVAL, "NULL handle");
+  if (!u || ((q_el == nullptr) == (b_nodal == nullptr)))
+    return fail(h, STMG_EINVAL, "need u and exactly one of q_el / b_nodal");
+  Level& L = h->lev[0];
+  if (q_el) CKS(assemble_into(h, q_el, L.b));
+  else CKS(copy_in(h, L.b, L.pitch, b_nodal, L.NT + 1, L.N + 1));
+  if (warm) CKS(copy_in(h, L.u, L.pitch, u, L.NT + 1, L.N + 1));
+  stmg_status st = solve_loop(h, adj, warm != 0, cycles, relres);
+  if (st != STMG_OK && st != STMG_EDIVERGED && st != STMG_EMAXITER) return st;
+  CKS(copy_out(h, u, L.u, L.pitch, L.NT + 1, L.N + 1));
+  CK(cudaStreamSynchronize(h->s));
+  if (st == STMG_EDIVERGED) fail(h, st, "relative residual exceeded div_tol");
+  if (st == STMG_EMAXITER) fail(h, st, "max_cycles reached before tol");
+  return st;
+}
+
+stmg_status stmg_solve(stmg_t h, const double* q_el, const double* b_nodal, double* u, int warm, int* cycles,
+                       double* relres) {
+  return solve_common(h, false, q_el, b_nodal, u, warm, cycles, relres);
+}
+
+stmg_status stmg_solve_adjoint(stmg_t h, const double* rhs, double* lam, int warm, int* cycles, double* relres) {
+  if (!rhs) return fail(h, STMG_EINVAL, "NULL rhs");
+  return solve_common(h, true, nullptr, rhs, lam, warm, cycles, relres);
+}
+
+stmg_status stmg_sensitivity(stmg_t h, const double* chi, const double* simp6, const double* u, const double* lam,
+                             double* g) {
+  if (!h) return fail(nullptr, STMG_EINVAL, "NULL handle");
+  if (!chi || !simp6 || !u || !lam || !g) return fail(h, STMG_EINVAL, "NULL array");
+  Level& L = h->lev[0];
+  const size_t need = 2 * (size_t)sens_chunks(L.NT) * L.N;
+  if (h->sens_n < need) {
+    dfree(h->sens);
+    h->sens_n = 0;
+    CKS(dalloc(h, &h->sens, need));
+    h->sens_n = need;
+  }
+  if (!h->gstage) CKS(dalloc(h, &h->gstage, 2 * (size_t)L.N));
+  CKS(copy_in(h, L.u, L.pitch, u, L.NT + 1, L.N + 1));
+  CKS(copy_in(h, L.t, L.pitch, lam, L.NT + 1, L.N + 1));
+  CK(cudaMemcpyAsync(h->gstage, chi, L.N * sizeof(double), cudaMemcpyDefault, h->s));
+  Simp6 sp;
+  for (int i = 0; i < 6; ++i) sp.v[i] = simp6[i];
+  CK(launch_sensitivity(L.N, L.NT, L.pitch, L.dx, L.dt, h->gstage, sp, L.u, L.t, h->sens, h->gstage + L.N, h->s));
+  CK(cudaMemcpyAsync(g, h->gstage + L.N, L.N * sizeof(double), cudaMemcpyDefault, h->s));
+  CK(cudaStreamSynchronize(h->s));
+  return STMG_OK;
+}
+
+stmg_status stmg_objective(stmg_t h, const double* b, const double* u, double theta_ref, double* theta) {
+  if (!h) return fail(nullptr, STMG_EINVAL, "NULL handle");
+  if (!b || !u || !theta || !(theta_ref != 0.0)) return fail(h, STMG_EINVAL, "bad stmg_objective arguments");
+  Level& L = h->lev[0];
+  CKS(copy_in(h, L.u, L.pitch, u, L.NT + 1, L.N + 1));
+  CKS(copy_in(h, L.t, L.pitch, b, L.NT + 1, L.N + 1));
+  CK(launch_dot(L.nvec, L.t, L.u, h->partials, h->scal, h->s));
+  double s = 0.0;
+  CKS(read_scalar(h, h->scal, &s));
+  *theta = s * L.dt / theta_ref;
+  return STMG_OK;
+}
+
+int stmg_num_levels(stmg_t h) { return h ? (int)h->lev.size() : 0; }
+
+stmg_status stmg_level_info(stmg_t h, int level, int* nel, int* nt, int* next, double* dx, double* dt,
+                            double* w_diri, double* lambda_eff) {
+  CKS(check_level(h, level));
+  const Level& L = h->lev[level];
+  if (nel) *nel = L.N;
+  if (nt) *nt = L.NT;
+  if (next) *next = L.next;
+  if (dx) *dx = L.dx;
+  if (dt) *dt = L.dt;
+  if (w_diri) *w_diri = L.W;
+  if (lambda_eff) *lambda_eff = L.lam;
+  return STMG_OK;
+}
+
+stmg_status stmg_level_material(stmg_t h, int level, double* k, double* c) {
+  CKS(check_level(h, level));
+  const Level& L = h->lev[level];
+  if (k) std::memcpy(k, L.k.data(), L.N * sizeof(double));
+  if (c) std::memcpy(c, L.c.data(), L.N * sizeof(double));
+  return STMG_OK;
+}
+
+stmg_status stmg_apply(stmg_t h, int level, int adjoint, const double* u, double* y) {
+  CKS(check_level(h, level));
+  if (!u || !y) return fail(h, STMG_EINVAL, "NULL array");
+  Level& L = h->lev[level];
+  CKS(ensure_fp64(h, L));
+  CKS(copy_in(h, L.u, L.pitch, u, L.NT + 1, L.N + 1));
+  CK(launch_apply<double>(view<double>(L, h->o.omega), adjoint != 0, L.u, L.t, h->s));
+  CKS(copy_out(h, y, L.t, L.pitch, L.NT + 1, L.N + 1));
+  CK(cudaStreamSynchronize(h->s));
+  return STMG_OK;
+}
+
+stmg_status stmg_smooth(stmg_t h, int level, int adjoint, int nsweeps, double* u, const double* b) {
+  CKS(check_level(h, level));
+  if (!u || !b || nsweeps < 0) return fail(h, STMG_EINVAL, "bad stmg_smooth arguments");
+  Level& L = h->lev[level];
+  CKS(ensure_fp64(h, L));
+  CKS(copy_in(h, L.u, L.pitch, u, L.NT + 1, L.N + 1));
+  CKS(copy_in(h, L.b, L.pitch, b, L.NT + 1, L.N + 1));
+  CKS(smooth_level<double>(h, L, adjoint != 0, nsweeps));
+  CKS(copy_out(h, u, L.u, L.pitch, L.NT + 1, L.N + 1));
+  CK(cudaStreamSynchronize(h->s));
+  return STMG_OK;
+}
+
+stmg_status stmg_restrict(stmg_t h, int level, const double* r, double* bc) {
+  CKS(check_level(h, level));
+  if (level + 1 >= (int)h->lev.size()) return fail(h, STMG_EINVAL, "level %d is the coarsest", level);
+  if (!r || !bc) return fail(h, STMG_EINVAL, "NULL array");
+  Level& L = h->lev[level];
+  Level& C = h->lev[level + 1];
+  CKS(ensure_fp64(h, L));
+  CKS(ensure_fp64(h, C));
+  CKS(copy_in(h, L.t, L.pitch, r, L.NT + 1, L.N + 1));
+  CK(launch_restrict<double>(L.next, L.N, L.NT, L.pitch, L.t, C.N, C.NT, C.pitch, C.b, h->s));
+  CKS(copy_out(h, bc, C.b, C.pitch, C.NT + 1, C.N + 1));
+  CK(cudaStreamSynchronize(h->s));
+  return STMG_OK;
+}
+
+stmg_status stmg_prolong_add(stmg_t h, int level, const double* z, double* u) {
+  CKS(check_level(h, level));
+  if (level + 1 >= (int)h->lev.size()) return fail(h, STMG_EINVAL, "level %d is the coarsest", level);
+  if (!z || !u) return fail(h, STMG_EINVAL, "NULL array");
+  Level& L = h->lev[level];
+  Level& C = h->lev[level + 1];
+  CKS(ensure_fp64(h, L));
+  CKS(ensure_fp64(h, C));
+  CKS(copy_in(h, C.u, C.pitch, z, C.NT + 1, C.N + 1));
+  CKS(copy_in(h, L.u, L.pitch, u, L.NT + 1, L.N + 1));
+  CK(launch_prolong_add<double>(L.next, L.N, L.NT, L.pitch, L.u, C.N, C.NT, C.pitch, C.u, h->s));
+  CKS(copy_out(h, u, L.u, L.pitch, L.NT + 1, L.N + 1));
+  CK(cudaStreamSynchronize(h->s));
+  return STMG_OK;
+}
+
+stmg_status stmg_exact_solve(stmg_t h, int level, int adjoint, const double* b, double* u) {
+  CKS(check_level(h, level));
+  if (!b || !u) return fail(h, STMG_EINVAL, "NULL array");
+  Level& L = h->lev[level];
+  if ((size_t)(L.N + 2) * 16 > 200 * 1024) return fail(h, STMG_EINVAL, "level too wide for the exact solver");
+  CKS(ensure_fp64(h, L));
+  CKS(copy_in(h, L.b, L.pitch, b, L.NT + 1, L.N + 1));
+  CK(launch_exact<double>(thomas_view(L), adjoint != 0, L.b, L.u, h->s));
+  CKS(copy_out(h, u, L.u, L.pitch, L.NT + 1, L.N + 1));
+  CK(cudaStreamSynchronize(h->s));
+  return STMG_OK;
+}
+
+stmg_status stmg_vcycle(stmg_t h, int adjoint, double* u, const double* b) {
+  if (!h) return fail(nullptr, STMG_EINVAL, "NULL handle");
+  if (!u || !b) return fail(h, STMG_EINVAL, "NULL array");
+  Level& L = h->lev[0];
+  CKS(copy_in(h, L.u, L.pitch, u, L.NT + 1, L.N + 1));
+  CKS(copy_in(h, L.b, L.pitch, b, L.NT + 1, L.N + 1));
+  if (h->o.precision == STMG_MIXED) {
+    CK(launch_defect(view<double>(L, h->o.omega), adjoint != 0, L.u, L.b, L.b32, h->partials, h->scal, h->s));
+    CK(cudaMemsetAsync(L.u32, 0, L.nvec * sizeof(float), h->s));
+    CKS(vcycle<float>(h, 0, adjoint != 0));
+    CK(launch_add_correction(L.nvec, L.u, L.u32, h->s));
+  } else {
+    CKS(vcycle<double>(h, 0, adjoint != 0));
+  }
+  CKS(copy_out(h, u, L.u, L.pitch, L.NT + 1, L.N + 1));
+  CK(cudaStreamSynchronize(h->s));
+  return STMG_OK;
+}
+
+}  // extern "C"
+
+extern "C" unsigned long long stmg_kernel_launches(void) { return launches_so_far(); }

@@ -1,0 +1,450 @@
+// stmg_kernels.cu -- CUDA kernels of the STMG V-cycle for sm_103a: damped Jacobi,
+// residual, restriction, prolongation, the exact time-stepping solve, deterministic
+// norms, coefficient/material/load set-up and the adjoint sensitivity.
+//
+// These are the per-DOF kernels; every space-time vector uses the padded layout of
+// stmg_internal.h.  Reductions are two-pass with a fixed grid and a fixed tree order,
+// so results do not depend on scheduling.
+#include <atomic>
+#include <type_traits>
+
+#include "stmg_internal.h"
+
+namespace stmg {
+
+static std::atomic<unsigned long long> g_launches{0};
+void count_launches(unsigned n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+unsigned long long launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
+
+namespace {
+
+constexpr int kThreads = 256;
+
+inline unsigned blocks_for(long long n, int threads = kThreads) {
+  long long b = (n + threads - 1) / threads;
+  return (unsigned)(b < 1 ? 1 : b);
+}
+
+// (J u) at DOF (n, i) of a level, p = n * pitch + i (Sec. 2.2 stencil, Appendix A).
+template <typename T>
+__device__ __forceinline__ T apply_at(const LevelView<T>& lv, bool adj, const T* __restrict__ u, int n, int i,
+                                      size_t p) {
+  if (n == 0 || i == 0) return lv.W * u[p];
+  const T* cf = lv.coef;
+  const int P = lv.pitch;
+  T acc = cf[kL * P + i] * u[p - 1];
+  acc = fma(cf[kD * P + i], u[p], acc);
+  acc = fma(cf[kU * P + i], u[p + 1], acc);
+  const bool has_prev = adj ? (n < lv.NT) : (n > 1);
+  if (has_prev) {
+    const size_t q = adj ? p + P : p - P;
+    acc = fma(cf[kPL * P + i], u[q - 1], acc);
+    acc = fma(cf[kPC * P + i], u[q], acc);
+    acc = fma(cf[kPR * P + i], u[q + 1], acc);
+  }
+  return acc;
+}
+
+// Damped Jacobi step (Sec. 3.1): uo = u + omega D^-1 (b - J u), D^-1 omega stored per node.
+template <typename T, bool ADJ>
+__global__ void __launch_bounds__(kThreads) k_jacobi(LevelView<T> lv, const T* __restrict__ u,
+                                                     const T* __restrict__ b, T* __restrict__ uo) {
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long total = (long long)(lv.NT + 1) * (lv.N + 1);
+  if (idx >= total) return;
+  const int n = (int)(idx / (lv.N + 1));
+  const int i = (int)(idx - (long long)n * (lv.N + 1));
+  const size_t p = (size_t)n * lv.pitch + i;
+  const T r = b[p] - apply_at(lv, ADJ, u, n, i, p);
+  const T w = (n == 0 || i == 0) ? lv.wW : lv.coef[kInvD * lv.pitch + i];
+  uo[p] = fma(w, r, u[p]);
+}
+
+// r = b - J u (MODE 0) or y = J u (MODE 1).
+template <typename T, bool ADJ, int MODE>
+__global__ void __launch_bounds__(kThreads) k_residual(LevelView<T> lv, const T* __restrict__ u,
+                                                       const T* __restrict__ b, T* __restrict__ r) {
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long total = (long long)(lv.NT + 1) * (lv.N + 1);
+  if (idx >= total) return;
+  const int n = (int)(idx / (lv.N + 1));
+  const int i = (int)(idx - (long long)n * (lv.N + 1));
+  const size_t p = (size_t)n * lv.pitch + i;
+  const T ju = apply_at(lv, ADJ, u, n, i, p);
+  r[p] = MODE == 0 ? b[p] - ju : ju;
+}
+
+// Restriction b_c = s P^T r (Sec. 3.1): x: 1/2 [1 2 1] within the row, s = 1;
+// t (causal): rows 2m and 2m+1, s = 1/2 (row 2m+1 absent past the last fine row).
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_restrict(int type, int Nf, int NTf, int pf, const T* __restrict__ r,
+                                                       int Nc, int NTc, int pc, T* __restrict__ bc) {
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long total = (long long)(NTc + 1) * (Nc + 1);
+  if (idx >= total) return;
+  const int m = (int)(idx / (Nc + 1));
+  const int j = (int)(idx - (long long)m * (Nc + 1));
+  T acc;
+  if (type == 1) {
+    const T* row = r + (size_t)m * pf;
+    acc = row[2 * j];
+    if (2 * j - 1 >= 0) acc += T(0.5) * row[2 * j - 1];
+    if (2 * j + 1 <= Nf) acc += T(0.5) * row[2 * j + 1];
+  } else {
+    acc = r[(size_t)(2 * m) * pf + j];
+    if (2 * m + 1 <= NTf) acc += r[(size_t)(2 * m + 1) * pf + j];
+    acc *= T(0.5);
+  }
+  bc[(size_t)m * pc + j] = acc;
+}
+
+// u += P z (Sec. 3.1): x: fine node 2j gets z_j, node 2j+1 gets (z_j + z_{j+1}) / 2;
+// t (causal): fine rows 2m and 2m+1 get coarse row m.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_prolong_add(int type, int Nf, int NTf, int pf, T* __restrict__ u,
+                                                          int Nc, int NTc, int pc, const T* __restrict__ z) {
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long total = (long long)(NTf + 1) * (Nf + 1);
+  if (idx >= total) return;
+  const int n = (int)(idx / (Nf + 1));
+  const int i = (int)(idx - (long long)n * (Nf + 1));
+  T add;
+  if (type == 1) {
+    const T* zr = z + (size_t)n * pc;
+    add = (i & 1) ? T(0.5) * (zr[i >> 1] + zr[(i >> 1) + 1]) : zr[i >> 1];
+  } else {
+    add = z[(size_t)(n >> 1) * pc + i];
+  }
+  u[(size_t)n * pf + i] += add;
+}
+
+// Exact solve of J u = b (or J^T u = b) by implicit time stepping: Dirichlet DOFs
+// u = b / W; then for each step a Thomas solve of (M/dt + K)_int T_n = f_n with
+// f_n = b_n - (coupling to the previous step), forward in time for J and backward for
+// J^T.  Arithmetic in FP64 whatever the storage type.  One block; thread 0 runs the
+// sequential recurrence, the other threads fill the Dirichlet DOFs.
+template <typename T>
+__global__ void k_exact(ThomasView tv, bool adj, const T* __restrict__ b, T* __restrict__ u) {
+  extern __shared__ double sm[];
+  const int N = tv.N, NT = tv.NT, P = tv.pitch;
+  for (int i = threadIdx.x; i <= N; i += blockDim.x) u[i] = (T)((double)b[i] / tv.W);
+  for (int n = 1 + threadIdx.x; n <= NT; n += blockDim.x) u[(size_t)n * P] = (T)((double)b[(size_t)n * P] / tv.W);
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  // FP64 rows: prev (previous step, node 0 = 0 since its column is eliminated) and cur.
+  double* prev = sm;
+  double* cur = sm + (N + 2);
+  for (int i = 0; i <= N + 1; ++i) prev[i] = 0.0;
+  cur[0] = 0.0;
+  cur[N + 1] = 0.0;
+  for (int step = 1; step <= NT; ++step) {
+    const int n = adj ? NT + 1 - step : step;
+    const bool has_prev = adj ? (n < NT) : (n > 1);
+    const T* bn = b + (size_t)n * P;
+    // forward elimination (cur holds the modified right-hand side)
+    double dp = 0.0;
+    for (int i = 1; i <= N; ++i) {
+      double f = (double)bn[i];
+      if (has_prev) f -= tv.pl[i] * prev[i - 1] + tv.pc[i] * prev[i] + tv.pr[i] * prev[i + 1];
+      dp = (f - tv.lo[i] * dp) * tv.inv[i];
+      cur[i] = dp;
+    }
+    // back substitution
+    for (int i = N - 1; i >= 1; --i) cur[i] = cur[i] - tv.cp[i] * cur[i + 1];
+    T* un = u + (size_t)n * P;
+    for (int i = 1; i <= N; ++i) {
+      un[i] = (T)cur[i];
+      prev[i] = cur[i];
+    }
+  }
+}
+
+// Block-level deterministic sum of one double per thread; result valid in thread 0.
+template <int BLOCK>
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double red[BLOCK];
+  red[threadIdx.x] = v;
+  __syncthreads();
+#pragma unroll
+  for (int w = BLOCK / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  return red[0];
+}
+
+// Squared norm of r = b - J u (u null: r = b), optionally storing r as R.
+template <typename T, typename R, bool ADJ>
+__global__ void __launch_bounds__(kThreads) k_resnorm(LevelView<T> lv, const T* __restrict__ u,
+                                                      const T* __restrict__ b, R* __restrict__ r_out,
+                                                      double* __restrict__ partials) {
+  const long long total = (long long)(lv.NT + 1) * (lv.N + 1);
+  double acc = 0.0;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int n = (int)(idx / (lv.N + 1));
+    const int i = (int)(idx - (long long)n * (lv.N + 1));
+    const size_t p = (size_t)n * lv.pitch + i;
+    const T r = u ? b[p] - apply_at(lv, ADJ, u, n, i, p) : b[p];
+    if (r_out) r_out[p] = (R)r;
+    acc = fma((double)r, (double)r, acc);
+  }
+  const double s = block_sum<kThreads>(acc);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+__global__ void k_final_sum(const double* __restrict__ partials, int n, double* __restrict__ out) {
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) acc += partials[i];
+  const double s = block_sum<1024>(acc);
+  if (threadIdx.x == 0) out[0] = s;
+}
+
+__global__ void __launch_bounds__(kThreads) k_dot(size_t n, const double* __restrict__ a,
+                                                  const double* __restrict__ b, double* __restrict__ partials) {
+  double acc = 0.0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    acc = fma(a[i], b[i], acc);
+  const double s = block_sum<kThreads>(acc);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(kThreads) k_add_correction(size_t n, double* __restrict__ u,
+                                                             const float* __restrict__ e) {
+  const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i < n) u[i] += (double)e[i];
+}
+
+// Stencil coefficients per node from element k, c (Sec. 2.2 element matrices, Appendix A).
+// m_e = c_e dx / (6 dt) and s_e = k_e / dx; node i touches elements i-1 and i.
+__global__ void k_build_coef(int N, int pitch, double dx, double dt, double W, double omega,
+                             const double* __restrict__ k, const double* __restrict__ c, double* __restrict__ cf64,
+                             float* __restrict__ cf32) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= pitch) return;
+  double v[kNumCoef] = {0, 0, 0, 0, 0, 0, 0, 0};
+  if (i == 0) {
+    v[kD] = W;
+    v[kInvD] = omega / W;
+  } else if (i <= N) {
+    const double ml = c[i - 1] * dx / (6.0 * dt), sl = k[i - 1] / dx;
+    const double mr = i < N ? c[i] * dx / (6.0 * dt) : 0.0, sr = i < N ? k[i] / dx : 0.0;
+    v[kL] = i >= 2 ? ml - sl : 0.0;
+    v[kU] = i < N ? mr - sr : 0.0;
+    v[kD] = 2.0 * ml + sl + 2.0 * mr + sr;
+    v[kPL] = i >= 2 ? -ml : 0.0;
+    v[kPC] = -2.0 * (ml + mr);
+    v[kPR] = i < N ? -mr : 0.0;
+    v[kInvD] = omega / v[kD];
+  }
+#pragma unroll
+  for (int s = 0; s < kNumCoef; ++s) {
+    if (cf64) cf64[(size_t)s * pitch + i] = v[s];
+    if (cf32) cf32[(size_t)s * pitch + i] = (float)v[s];
+  }
+}
+
+// SIMP (Sec. 2.1).
+__global__ void k_simp(int N, const double* __restrict__ chi, Simp6 sp, double* __restrict__ k,
+                       double* __restrict__ c) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= N) return;
+  const double x = chi[e];
+  k[e] = sp.v[0] + (sp.v[1] - sp.v[0]) * pow(x, sp.v[4]);
+  c[e] = sp.v[2] + (sp.v[3] - sp.v[2]) * pow(x, sp.v[5]);
+}
+
+// b = B b_Neu with b_Neu,i = dx/2 (q_{i-1} + q_i) for element-wise constant q.
+__global__ void __launch_bounds__(kThreads) k_assemble_load(int N, int NT, int pitch, double dx,
+                                                            const double* __restrict__ q, double* __restrict__ b) {
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long total = (long long)(NT + 1) * pitch;
+  if (idx >= total) return;
+  const int n = (int)(idx / pitch);
+  const int i = (int)(idx - (long long)n * pitch);
+  double v = 0.0;
+  if (n >= 1 && i >= 1 && i <= N) {
+    const double* qn = q + (size_t)n * N;
+    v = 0.5 * dx * (qn[i - 1] + (i < N ? qn[i] : 0.0));
+  }
+  b[idx] = v;
+}
+
+// Sensitivity partial sums over a chunk of time levels for element e (Sec. 7.2):
+//   S_k = sum_n (lam_e - lam_{e+1}) (u_e - u_{e+1}) / dx
+//   S_c = sum_n dx/(6 dt) [lam_e (2 d_e + d_{e+1}) + lam_{e+1} (d_e + 2 d_{e+1})],
+// d_j = u[n][j] - u[n-1][j] (the n-1 term only for n >= 2); node 0 values are masked.
+__global__ void k_sens_partial(int N, int NT, int pitch, double dx, double dt, const double* __restrict__ u,
+                               const double* __restrict__ lam, double* __restrict__ scratch) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const int chunk = blockIdx.y;
+  if (e >= N) return;
+  const int n0 = max(1, chunk * kSensRowsPerChunk), n1 = min(NT, (chunk + 1) * kSensRowsPerChunk - 1);
+  double sk = 0.0, sc = 0.0;
+  for (int n = n0; n <= n1; ++n) {
+    const double* un = u + (size_t)n * pitch;
+    const double* ln = lam + (size_t)n * pitch;
+    const double ue = e == 0 ? 0.0 : un[e], ue1 = un[e + 1];
+    const double le = e == 0 ? 0.0 : ln[e], le1 = ln[e + 1];
+    double de = ue, de1 = ue1;
+    if (n >= 2) {
+      const double* up = un - pitch;
+      de -= e == 0 ? 0.0 : up[e];
+      de1 -= up[e + 1];
+    }
+    sk = fma(le - le1, ue - ue1, sk);
+    sc = fma(le, 2.0 * de + de1, sc);
+    sc = fma(le1, de + 2.0 * de1, sc);
+  }
+  const int chunks = gridDim.y;
+  scratch[(size_t)chunk * N + e] = sk / dx;
+  scratch[(size_t)(chunks + chunk) * N + e] = sc * dx / (6.0 * dt);
+}
+
+__global__ void k_sens_final(int N, int chunks, const double* __restrict__ chi, Simp6 sp,
+                             const double* __restrict__ scratch, double* __restrict__ g) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= N) return;
+  double sk = 0.0, sc = 0.0;
+  for (int q = 0; q < chunks; ++q) {
+    sk += scratch[(size_t)q * N + e];
+    sc += scratch[(size_t)(chunks + q) * N + e];
+  }
+  const double x = chi[e];
+  const double dk = sp.v[4] * (sp.v[1] - sp.v[0]) * pow(x, sp.v[4] - 1.0);
+  const double dc = sp.v[5] * (sp.v[3] - sp.v[2]) * pow(x, sp.v[5] - 1.0);
+  g[e] = -(dk * sk + dc * sc);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------ launchers
+
+template <typename T>
+cudaError_t launch_jacobi(const LevelView<T>& lv, bool adj, const T* u, const T* b, T* uo, cudaStream_t s) {
+  const unsigned g = blocks_for((long long)(lv.NT + 1) * (lv.N + 1));
+  if (adj) k_jacobi<T, true><<<g, kThreads, 0, s>>>(lv, u, b, uo);
+  else k_jacobi<T, false><<<g, kThreads, 0, s>>>(lv, u, b, uo);
+  count_launches(2);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_residual(const LevelView<T>& lv, bool adj, const T* u, const T* b, T* r, cudaStream_t s) {
+  const unsigned g = blocks_for((long long)(lv.NT + 1) * (lv.N + 1));
+  if (adj) k_residual<T, true, 0><<<g, kThreads, 0, s>>>(lv, u, b, r);
+  else k_residual<T, false, 0><<<g, kThreads, 0, s>>>(lv, u, b, r);
+  count_launches(2);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_apply(const LevelView<T>& lv, bool adj, const T* u, T* y, cudaStream_t s) {
+  const unsigned g = blocks_for((long long)(lv.NT + 1) * (lv.N + 1));
+  if (adj) k_residual<T, true, 1><<<g, kThreads, 0, s>>>(lv, u, nullptr, y);
+  else k_residual<T, false, 1><<<g, kThreads, 0, s>>>(lv, u, nullptr, y);
+  count_launches(2);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_restrict(int type, int Nf, int NTf, int pf, const T* r, int Nc, int NTc, int pc, T* bc,
+                            cudaStream_t s) {
+  k_restrict<T><<<blocks_for((long long)(NTc + 1) * (Nc + 1)), kThreads, 0, s>>>(type, Nf, NTf, pf, r, Nc, NTc,
+                                                                                   pc, bc);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_prolong_add(int type, int Nf, int NTf, int pf, T* u, int Nc, int NTc, int pc, const T* z,
+                               cudaStream_t s) {
+  k_prolong_add<T><<<blocks_for((long long)(NTf + 1) * (Nf + 1)), kThreads, 0, s>>>(type, Nf, NTf, pf, u, Nc, NTc,
+                                                                                      pc, z);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_exact(const ThomasView& tv, bool adj, const T* b, T* u, cudaStream_t s) {
+  const size_t smem = sizeof(double) * 2 * (size_t)(tv.N + 2);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_exact<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_exact<T><<<1, 256, smem, s>>>(tv, adj, b, u);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+template <typename T, typename R>
+cudaError_t launch_resnorm(const LevelView<T>& lv, bool adj, const T* u, const T* b, R* r_out, double* partials,
+                           double* out, cudaStream_t s) {
+  if (adj) k_resnorm<T, R, true><<<kNormBlocks, kThreads, 0, s>>>(lv, u, b, r_out, partials);
+  else k_resnorm<T, R, false><<<kNormBlocks, kThreads, 0, s>>>(lv, u, b, r_out, partials);
+  k_final_sum<<<1, 1024, 0, s>>>(partials, kNormBlocks, out);
+  count_launches(3);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_defect(const LevelView<double>& lv, bool adj, const double* u, const double* b, float* r32,
+                          double* partials, double* out, cudaStream_t s) {
+  return launch_resnorm<double, float>(lv, adj, u, b, r32, partials, out, s);
+}
+
+cudaError_t launch_add_correction(size_t n, double* u, const float* e, cudaStream_t s) {
+  k_add_correction<<<blocks_for((long long)n), kThreads, 0, s>>>(n, u, e);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dot(size_t n, const double* a, const double* b, double* partials, double* out, cudaStream_t s) {
+  k_dot<<<kNormBlocks, kThreads, 0, s>>>(n, a, b, partials);
+  k_final_sum<<<1, 1024, 0, s>>>(partials, kNormBlocks, out);
+  count_launches(2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_build_coef(int N, int pitch, double dx, double dt, double W, double omega, const double* k,
+                              const double* c, double* coef64, float* coef32, cudaStream_t s) {
+  k_build_coef<<<blocks_for(pitch), kThreads, 0, s>>>(N, pitch, dx, dt, W, omega, k, c, coef64, coef32);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_simp(int N, const double* chi, Simp6 sp, double* k, double* c, cudaStream_t s) {
+  k_simp<<<blocks_for(N), kThreads, 0, s>>>(N, chi, sp, k, c);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_assemble_load(int N, int NT, int pitch, double dx, const double* q, double* b, cudaStream_t s) {
+  k_assemble_load<<<blocks_for((long long)(NT + 1) * pitch), kThreads, 0, s>>>(N, NT, pitch, dx, q, b);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sensitivity(int N, int NT, int pitch, double dx, double dt, const double* chi, Simp6 sp,
+                               const double* u, const double* lam, double* scratch, double* g, cudaStream_t s) {
+  const int chunks = sens_chunks(NT);
+  dim3 grid(blocks_for(N, 128), chunks);
+  k_sens_partial<<<grid, 128, 0, s>>>(N, NT, pitch, dx, dt, u, lam, scratch);
+  k_sens_final<<<blocks_for(N), kThreads, 0, s>>>(N, chunks, chi, sp, scratch, g);
+  count_launches(2);
+  return cudaGetLastError();
+}
+
+#define STMG_INST(T)                                                                                            \
+  template cudaError_t launch_jacobi<T>(const LevelView<T>&, bool, const T*, const T*, T*, cudaStream_t);       \
+  template cudaError_t launch_residual<T>(const LevelView<T>&, bool, const T*, const T*, T*, cudaStream_t);     \
+  template cudaError_t launch_apply<T>(const LevelView<T>&, bool, const T*, T*, cudaStream_t);                  \
+  template cudaError_t launch_restrict<T>(int, int, int, int, const T*, int, int, int, T*, cudaStream_t);       \
+  template cudaError_t launch_prolong_add<T>(int, int, int, int, T*, int, int, int, const T*, cudaStream_t);    \
+  template cudaError_t launch_exact<T>(const ThomasView&, bool, const T*, T*, cudaStream_t);                    \
+  template cudaError_t launch_resnorm<T, T>(const LevelView<T>&, bool, const T*, const T*, T*, double*, double*, \
+                                            cudaStream_t);
+STMG_INST(double)
+STMG_INST(float)
+#undef STMG_INST
+
+}  // namespace stmg

@@ -125,7 +125,7 @@ def config4(N=1024, NT=4096):
     chi = 0.05 + 0.95 * uniform(4, N)
     fd = np.sort(np.floor(uniform(5, 32) * N).astype(np.int64))
     return dict(name="config4", N=N, NT=NT, L=1.0, tT=1.0, chi=chi, simp=simp_params(1e-3, 1.0, 1.0, 1.0),
-                k=None, c=None, q=load_uniform(N, NT), fd_elements=fd, theta_ref=1.0, tol=1e-10)
+                k=None, c=None, q=load_uniform(N, NT), fd_elements=fd, theta_ref=1.0, tol=1e-10, nu=20)
 
 
 def _round64(v):

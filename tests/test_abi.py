@@ -1,0 +1,45 @@
+"""The C-ABI library loads and exports every function that include/stmg.h declares (CPU only)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2505_10168_gb300 import _binding
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(stmg_[a-z0-9_]+)\s*\(", src))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = ctypes.CDLL(_binding.LIB_PATH)
+    declared = _declared()
+    assert len(declared) >= 20
+    missing = [n for n in sorted(declared) if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_signatures_cover_the_header():
+    assert _declared() <= set(_binding._SIGS)
+
+
+def test_default_opts_and_errors_without_gpu():
+    lib = _binding.lib()
+    o = _binding.make_opts()
+    assert (o.nu, o.omega, o.lambda_crit, o.max_cycles, o.tol) == (5, 0.5, 0.25, 100, 1e-10)
+    h = ctypes.c_void_p()
+    # invalid sizes are rejected on the host before any device work
+    st = lib.stmg_create(ctypes.byref(h), 0, 4, 1.0, 1.0, None, None, None, None)
+    assert _binding.STATUS[st] == "einval" and not h.value
+    assert b"nel" in lib.stmg_last_error(None)
+    with pytest.raises(_binding.STMGError):
+        _binding.make_opts(no_such_option=1)
