@@ -158,6 +158,32 @@ stmg_status stmg_exact_solve(stmg_t handle, int level, int adjoint, const double
  * the options (STMG_MIXED: one FP64 defect-correction step around one FP32 cycle). */
 stmg_status stmg_vcycle(stmg_t handle, int adjoint, double* u, const double* b);
 
+/* ---- allocation-free sensitivity ------------------------------------------------------ */
+/* The paper has no counterpart to this entry point; it is a deployment variant of
+ * stmg_sensitivity for callers that cannot allocate device memory when they need a
+ * gradient: cudaMalloc/cudaFree may synchronise the whole device, which a caller that
+ * overlaps its own streams with ours cannot afford, and a caller whose device memory is
+ * fixed at start-up (a framework-owned pool or a hard budget) may not request more.
+ *
+ * Same result as stmg_sensitivity, without a handle and without any allocation:
+ * nel, nt, L, t_end describe the grid as in stmg_create; chi (nel), u and lam
+ * ((nt+1) x (nel+1), dense rows) and dtheta_dchi (nel) must all be device memory of the
+ * current device (host arrays are rejected with STMG_EINVAL, since staging them would
+ * need an allocation); simp6 is a host array as in stmg_simp; stream may be NULL.
+ * The partial sums live in one fixed array of STMG_NOALLOC_MAX_SCRATCH doubles (8 MiB)
+ * inside the library's device image, which every GPU that loads the library keeps until
+ * the process exits.  The call needs 2 * ceil((nt+1)/256) * nel of them and rejects
+ * larger problems with STMG_EINVAL (for example nel = 4096 with nt up to 32767).
+ * The first call on each device looks up that array's device address; make it before
+ * any stream capture.  All calls share the array: calls whose work overlaps on the GPU
+ * (different streams or host threads without ordering) race and give wrong results, so
+ * serialise them.  Every scratch value read is written earlier in the same call, so a
+ * previous call's contents never leak into a result.  Returns after dtheta_dchi is
+ * complete; messages go to stmg_last_error(NULL). */
+#define STMG_NOALLOC_MAX_SCRATCH (1 << 20)
+stmg_status stmg_sensitivity_noalloc(int nel, int nt, double L, double t_end, const double* chi, const double* simp6,
+                                     const double* u, const double* lam, double* dtheta_dchi, void* stream);
+
 /* ---- statistics ------------------------------------------------------------------------ */
 /* Number of CUDA kernels this library has launched in this process so far (all handles). */
 unsigned long long stmg_kernel_launches(void);

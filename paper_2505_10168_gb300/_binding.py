@@ -70,6 +70,7 @@ _SIGS = {
     "stmg_prolong_add": (_i, [_vp, _i, _vp, _vp]),
     "stmg_exact_solve": (_i, [_vp, _i, _i, _vp, _vp]),
     "stmg_vcycle": (_i, [_vp, _i, _vp, _vp]),
+    "stmg_sensitivity_noalloc": (_i, [_i, _i, _d, _d, _vp, _dp, _vp, _vp, _vp, _vp]),
     "stmg_kernel_launches": (C.c_ulonglong, []),
 }
 

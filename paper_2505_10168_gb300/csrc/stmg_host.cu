@@ -791,3 +791,7 @@ stmg_status stmg_vcycle(stmg_t h, int adjoint, double* u, const double* b) {
 }  // extern "C"
 
 extern "C" unsigned long long stmg_kernel_launches(void) { return launches_so_far(); }
+
+namespace stmg {
+void set_global_error(const char* msg) { g_global_error = msg; }
+}  // namespace stmg

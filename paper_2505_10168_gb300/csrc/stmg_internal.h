@@ -52,6 +52,9 @@ struct ThomasView {
   double W;
 };
 
+// Sets the message returned by stmg_last_error(NULL) on this host thread.
+void set_global_error(const char* msg);
+
 // Process-wide count of kernels launched by the library (stmg_kernel_launches).
 void count_launches(unsigned n);
 unsigned long long launches_so_far();
