@@ -44,6 +44,7 @@ def parse():
     p.add_argument("--workload", default="config2", choices=["config1", "config2", "config3", "config4"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-variant", action="store_true", help="skip the other-precision solve of the same workload")
     return p.parse_args()
 
 
@@ -290,10 +291,10 @@ def main():
         e[3].record(stream)
         torch.cuda.synchronize()
         sweep_ms = (e[2].elapsed_time(e[3]) - e[0].elapsed_time(e[1])) / nsw
-        flops = 15.0 * dofs  # 7 FMA + 1 subtraction per DOF
+        flops = 12.0 * dofs  # 6 FMA per DOF: u <- (1 - w) u + b' + sum of 5 scaled neighbours
         bytes_alg = 24.0 * dofs  # read u, b; write u (FP64)
         ach = flops / (sweep_ms * 1e-3) / 1e12
-        roofline = {"kernel": "k_jacobi<double> (finest level)", "bound": "alu", "achieved": ach,
+        roofline = {"kernel": "k_sweep<double> (finest level)", "bound": "alu", "achieved": ach,
                     "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s", "frac": ach / NOMINAL_FP64_TFLOPS,
                     "traffic": None, "ms_per_launch": sweep_ms,
                     "hbm_gbs": bytes_alg / (sweep_ms * 1e-3) / 1e9,
@@ -325,6 +326,27 @@ def main():
                "d2h_bytes_per_step": int(uh.numel() * 8 + 8 * (cycles + 2)), "steps": ksteps}
         del qh, uh
 
+    # ---- the other precision on the same workload (same metric, same tolerance) ----
+    variant = None
+    if not args.no_variant:
+        other = "mixed" if args.precision == "fp64" else "fp64"
+        s2 = pkg.Solver(N, NT, L, tT, k, c, precision=other, tol=TOL)
+        for _ in range(max(1, args.warmup)):
+            s2.solve(u, q=q)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st2 = [s2.solve(u, q=q) for _ in range(args.steps)]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms2 = e0.elapsed_time(e1) / args.steps
+        variant = {"precision": other, "value": world * dofs / (ms2 * 1e-3), "unit": "DOF/s", "ms_per_step": ms2,
+                   "cycles": st2[-1][1], "relres": st2[-1][2],
+                   "converged": all(x[0] == "ok" and x[2] < TOL for x in st2),
+                   "dtype": "f64" if other == "fp64" else "f32+f64"}
+        s2.close()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_obj(w)
@@ -341,7 +363,7 @@ def main():
                        "l2": "no flush: every vector (%d MB) exceeds the 129 MB L2" % (dofs * 8 // 2 ** 20),
                        "parallelism": "replicas" if world > 1 else "single"},
             "clocks": clocks, "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline,
-            "cpu_baseline": cpu,
+            "cpu_baseline": cpu, "variant": variant,
         }
         print(json.dumps(out))
     if world > 1:

@@ -129,6 +129,21 @@ stmg_status stmg_solve_adjoint(stmg_t handle, const double* rhs, double* lam, in
 stmg_status stmg_sensitivity(stmg_t handle, const double* chi, const double* simp6, const double* u,
                              const double* lam, double* dtheta_dchi);
 
+/* ---- time-slab checkpointing of the forward state ------------------------------------ */
+/* J is block lower-bidiagonal (Sec. 2.2): every time level of the forward solution follows
+ * from the previous one by one implicit step.  A caller that keeps only every K-th time
+ * level of a solution (the checkpoints: rows 0, K, 2K, ..., (S-1)K with S = ceil(nt/K),
+ * stored as S dense rows of nel+1 values) can rebuild the rest exactly.
+ * stmg_recompute_slabs fills u ((nt+1) x (nel+1)) with the checkpoint rows and, for each
+ * slab j, rows jK+1 .. min((j+1)K, nt) stepped from row jK with right-hand side b_nodal;
+ * all slabs run concurrently.  Requires nel <= 8192. */
+stmg_status stmg_recompute_slabs(stmg_t handle, const double* b_nodal, const double* ckpt, int slab_rows,
+                                 double* u);
+/* The design sensitivity of stmg_sensitivity, with u recomputed slab by slab from the
+ * checkpoints inside the same kernel instead of being read from a stored solution. */
+stmg_status stmg_sensitivity_slabs(stmg_t handle, const double* chi, const double* simp6, const double* b_nodal,
+                                   const double* ckpt, int slab_rows, const double* lam, double* dtheta_dchi);
+
 /* Theta = b^T u dt / theta_ref (Sec. 7.1); theta: host output. */
 stmg_status stmg_objective(stmg_t handle, const double* b, const double* u, double theta_ref, double* theta);
 

@@ -105,6 +105,18 @@ class Solver:
         B.check(B.lib().stmg_sensitivity(self._h, B.ptr(chi), s, B.ptr(u), B.ptr(lam), B.ptr(g)), self._h)
         return g
 
+    def recompute_slabs(self, b, ckpt, slab_rows, u):
+        """Fill u from checkpoint rows 0, K, 2K, ... by exact time stepping per slab."""
+        B.check(B.lib().stmg_recompute_slabs(self._h, B.ptr(b), B.ptr(ckpt), int(slab_rows), B.ptr(u)), self._h)
+        return u
+
+    def sensitivity_slabs(self, chi, simp6, b, ckpt, slab_rows, lam, g):
+        """Sensitivity with the forward state recomputed from checkpoints."""
+        s = (C.c_double * 6)(*[float(v) for v in simp6])
+        B.check(B.lib().stmg_sensitivity_slabs(self._h, B.ptr(chi), s, B.ptr(b), B.ptr(ckpt), int(slab_rows),
+                                                B.ptr(lam), B.ptr(g)), self._h)
+        return g
+
     def objective(self, b, u, theta_ref=1.0):
         out = C.c_double(0.0)
         B.check(B.lib().stmg_objective(self._h, B.ptr(b), B.ptr(u), float(theta_ref), C.byref(out)), self._h)

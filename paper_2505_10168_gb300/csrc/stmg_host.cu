@@ -13,6 +13,8 @@
 
 #include "stmg.h"
 #include "stmg_internal.h"
+#include "stmg_slab.h"
+#include "stmg_stream.h"
 
 using namespace stmg;
 
@@ -31,7 +33,7 @@ struct Level {
   double* dc = nullptr;
   double* cf64 = nullptr;    // kNumCoef * pitch
   float* cf32 = nullptr;
-  double* th = nullptr;      // Thomas factors: 6 arrays of N+2 doubles
+  double* th = nullptr;      // Thomas factors: 8 arrays of N+2 doubles
   double *u = nullptr, *b = nullptr, *t = nullptr;    // FP64 vectors
   float *u32 = nullptr, *b32 = nullptr, *t32 = nullptr;  // FP32 vectors (mixed precision)
 };
@@ -52,6 +54,11 @@ struct stmg_handle {
   double* sens = nullptr;      // sensitivity scratch
   size_t sens_n = 0;
   double* gstage = nullptr;    // element-array staging (chi, gradient)
+  // CUDA graphs of one solver iteration, per [precision][adjoint]; captured on cs.
+  cudaStream_t cs = nullptr;
+  cudaGraphExec_t gexec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  unsigned gkernels[2][2] = {{0, 0}, {0, 0}};  // kernels per graph (launch statistics)
+  double* graph_u0 = nullptr;  // level-0 u buffer that the FP64 graphs expect to hold u
   std::string err;
 };
 
@@ -193,7 +200,7 @@ std::vector<Level> plan_levels(const stmg_opts& o, int N, int NT, double Ldom, d
 void thomas_factors(const Level& L, std::vector<double>& out) {
   const int N = L.N;
   const size_t S = N + 2;
-  out.assign(6 * S, 0.0);
+  out.assign(8 * S, 0.0);
   double* lo = &out[0];
   double* inv = &out[S];
   double* cp = &out[2 * S];
@@ -212,11 +219,15 @@ void thomas_factors(const Level& L, std::vector<double>& out) {
     pr[i] = i < N ? -mr : 0.0;
   }
   double cprev = 0.0;
+  double* alpha = &out[6 * S];
+  double* beta = &out[7 * S];
   for (int i = 1; i <= N; ++i) {
     const double den = di[i] - lo[i] * cprev;
     inv[i] = 1.0 / den;
     cp[i] = up[i] * inv[i];
     cprev = cp[i];
+    alpha[i] = -lo[i] * inv[i];
+    beta[i] = -cp[i];
   }
 }
 
@@ -227,7 +238,7 @@ stmg_status setup_level(stmg_t h, Level& L) {
   if (!L.dc) CKS(dalloc(h, &L.dc, L.N));
   if (!L.cf64) CKS(dalloc(h, &L.cf64, (size_t)kNumCoef * L.pitch));
   if (!L.cf32) CKS(dalloc(h, &L.cf32, (size_t)kNumCoef * L.pitch));
-  if (!L.th) CKS(dalloc(h, &L.th, 6 * (size_t)(L.N + 2)));
+  if (!L.th) CKS(dalloc(h, &L.th, 8 * (size_t)(L.N + 2)));
   CK(cudaMemcpyAsync(L.dk, L.k.data(), L.N * sizeof(double), cudaMemcpyHostToDevice, h->s));
   CK(cudaMemcpyAsync(L.dc, L.c.data(), L.N * sizeof(double), cudaMemcpyHostToDevice, h->s));
   CK(launch_build_coef(L.N, L.pitch, L.dx, L.dt, L.W, h->o.omega, L.dk, L.dc, L.cf64, L.cf32, h->s));
@@ -273,16 +284,28 @@ template <typename T>
 LevelView<T> view(const Level& L, double omega);
 template <>
 LevelView<double> view<double>(const Level& L, double omega) {
-  return LevelView<double>{L.N, L.NT, L.pitch, L.cf64, L.W, omega / L.W};
+  return LevelView<double>{L.N, L.NT, L.pitch, make_fastdiv(L.N + 1), L.cf64, L.W, omega, 1.0 - omega,
+                           omega / L.W, L.W / omega};
 }
 template <>
 LevelView<float> view<float>(const Level& L, double omega) {
-  return LevelView<float>{L.N, L.NT, L.pitch, L.cf32, (float)L.W, (float)(omega / L.W)};
+  return LevelView<float>{L.N,          L.NT,           L.pitch,
+                          make_fastdiv(L.N + 1), L.cf32, (float)L.W,
+                          (float)omega, (float)(1.0 - omega), (float)(omega / L.W),
+                          (float)(L.W / omega)};
 }
 
-ThomasView thomas_view(const Level& L) {
+ThomasView thomas_view(const Level& L, double omega) {
   const size_t S = L.N + 2;
-  return ThomasView{L.N, L.NT, L.pitch, L.th, L.th + S, L.th + 2 * S, L.th + 3 * S, L.th + 4 * S, L.th + 5 * S, L.W};
+  return ThomasView{L.N,         L.NT,        L.pitch,     L.th, L.th + S, L.th + 2 * S, L.th + 3 * S,
+                    L.th + 4 * S, L.th + 5 * S, L.cf64 + (size_t)kDW * L.pitch, L.W, omega};
+}
+
+SlabView slab_view(const Level& L, double omega, int K) {
+  const size_t S = L.N + 2;
+  return SlabView{L.N,          L.NT,         L.pitch,      K,           L.dx,        L.dt,
+                  omega,        L.cf64 + (size_t)kDW * L.pitch, L.th + 3 * S, L.th + 4 * S, L.th + 5 * S,
+                  L.th + S,     L.th + 6 * S, L.th + 7 * S};
 }
 
 // Level vectors for precision T.
@@ -316,38 +339,136 @@ stmg_status smooth_level(stmg_t h, Level& L, bool adj, int nsweeps) {
   const LevelView<T> lv = view<T>(L, h->o.omega);
   for (int s = 0; s < nsweeps; ++s) {
     Vecs<T> v = vecs<T>(L);
-    CK(launch_jacobi<T>(lv, adj, v.u, v.b, v.t, h->s));
+    CK(launch_sweep<T>(lv, adj, v.u, v.b, v.t, h->s));
     set_u<T>(L, v.t);
     set_t<T>(L, v.u);
   }
   return STMG_OK;
 }
 
-// Alg. 1, VCycle(l, u, b), in precision T on the level's own u and b.
+// Alg. 1, VCycle(l, u, b), in precision T on the level's own u and (scaled) b.
+// zero_init: u starts at 0, so the first pre-smoothing step is exactly u = b' (a copy).
+// first_done: the caller already ran the first pre-smoothing step.
 template <typename T>
-stmg_status vcycle(stmg_t h, int l, bool adj) {
+stmg_status vcycle(stmg_t h, int l, bool adj, bool zero_init, bool first_done) {
   Level& L = h->lev[l];
   if (l == (int)h->lev.size() - 1) {
     Vecs<T> v = vecs<T>(L);
-    CK(launch_exact<T>(thomas_view(L), adj, v.b, v.u, h->s));
+    CK(launch_exact<T>(thomas_view(L, h->o.omega), adj, v.b, v.u, h->s));
     return STMG_OK;
   }
   Level& C = h->lev[l + 1];
-  CKS(smooth_level<T>(h, L, adj, h->o.nu));
+  int pre = h->o.nu;
+  if (zero_init && !first_done) {
+    Vecs<T> v = vecs<T>(L);
+    if (pre > 0) {
+      CK(cudaMemcpyAsync(v.u, v.b, L.nvec * sizeof(T), cudaMemcpyDeviceToDevice, h->s));
+      --pre;
+    } else {
+      CK(cudaMemsetAsync(v.u, 0, L.nvec * sizeof(T), h->s));
+    }
+  } else if (first_done) {
+    --pre;
+  }
+  CKS(smooth_level<T>(h, L, adj, pre));
   {
     Vecs<T> v = vecs<T>(L);
     Vecs<T> vc = vecs<T>(C);
     CK(launch_residual<T>(view<T>(L, h->o.omega), adj, v.u, v.b, v.t, h->s));
-    CK(launch_restrict<T>(L.next, L.N, L.NT, L.pitch, v.t, C.N, C.NT, C.pitch, vc.b, h->s));
-    CK(cudaMemsetAsync(vc.u, 0, C.nvec * sizeof(T), h->s));
+    CK(launch_restrict<T>(L.next, L.N, L.NT, L.pitch, v.t, view<T>(C, h->o.omega), vc.b, h->s));
   }
-  CKS(vcycle<T>(h, l + 1, adj));
+  CKS(vcycle<T>(h, l + 1, adj, true, false));
   {
     Vecs<T> v = vecs<T>(L);
     Vecs<T> vc = vecs<T>(C);
     CK(launch_prolong_add<T>(L.next, L.N, L.NT, L.pitch, v.u, C.N, C.NT, C.pitch, vc.u, h->s));
   }
   CKS(smooth_level<T>(h, L, adj, h->o.nu));
+  return STMG_OK;
+}
+
+// Split nu sweeps into passes of at most 5 fused sweeps.
+std::vector<int> sweep_passes(int nu) {
+  std::vector<int> p;
+  const int k = (nu + 4) / 5;
+  for (int i = 0; i < k; ++i) p.push_back(nu / k + (i < nu % k ? 1 : 0));
+  return p;
+}
+
+StreamArgs stream_args(const Level& L, double omega) {
+  StreamArgs a{};
+  a.N = L.N;
+  a.NT = L.NT;
+  a.pitch = L.pitch;
+  a.omega = (float)omega;
+  a.omc = (float)(1.0 - omega);
+  a.Wo = (float)(L.W / omega);
+  a.coef = L.cf32;
+  stream_layout(L.N, L.NT, a);
+  return a;
+}
+
+// Alg. 1 in FP32 with fused passes: on every level the nu pre-smoothing sweeps from a
+// zero start, the residual and the restriction run as one DOWN pass (or several when
+// nu > 5), and the prolongation plus the nu post-smoothing sweeps as one UP pass.  On the
+// finest level the result is added to the FP64 iterate u64 (mixed scheme) instead of
+// being stored.  The level's FP32 u pointer ends on the level's result.
+stmg_status vcycle32_fused(stmg_t h, int l, bool adj, double* u64) {
+  Level& L = h->lev[l];
+  if (l == (int)h->lev.size() - 1) {
+    CK(launch_exact<float>(thomas_view(L, h->o.omega), adj, L.b32, L.u32, h->s));
+    if (u64) CK(launch_add_correction(L.nvec, u64, L.u32, h->s));
+    return STMG_OK;
+  }
+  Level& C = h->lev[l + 1];
+  const std::vector<int> passes = sweep_passes(h->o.nu);
+  const bool xc = L.next == STMG_XCOARSEN;
+  // DOWN
+  float* in = nullptr;
+  float* out = L.u32;
+  for (size_t p = 0; p < passes.size(); ++p) {
+    StreamArgs a = stream_args(L, h->o.omega);
+    a.u_in = in;
+    a.zero_init = p == 0;
+    a.bs = L.b32;
+    a.u_out = out;
+    int mode = kStreamPlain;
+    if (p + 1 == passes.size()) {
+      mode = xc ? kStreamDownX : kStreamDownT;
+      a.pc = C.pitch;
+      a.ccoef = C.cf32;
+      a.cwW = (float)(h->o.omega / C.W);
+      a.bc = C.b32;
+    }
+    CK(launch_stream(mode, adj, passes[p], a, h->s));
+    in = out;
+    out = (out == L.u32) ? L.t32 : L.u32;
+  }
+  CKS(vcycle32_fused(h, l + 1, adj, nullptr));
+  // UP
+  for (size_t p = 0; p < passes.size(); ++p) {
+    StreamArgs a = stream_args(L, h->o.omega);
+    a.u_in = in;
+    a.zero_init = 0;
+    a.bs = L.b32;
+    const bool last = p + 1 == passes.size();
+    a.u_out = (last && u64) ? nullptr : out;
+    a.u64 = (last && u64) ? u64 : nullptr;
+    int mode = kStreamPlain;
+    if (p == 0) {
+      mode = xc ? kStreamUpX : kStreamUpT;
+      a.pc = C.pitch;
+      a.z = C.u32;
+    }
+    CK(launch_stream(mode, adj, passes[p], a, h->s));
+    if (!(last && u64)) {
+      in = out;
+      out = (out == L.u32) ? L.t32 : L.u32;
+    }
+  }
+  float* other = (in == L.u32) ? L.t32 : L.u32;
+  L.u32 = in;
+  L.t32 = other;
   return STMG_OK;
 }
 
@@ -395,22 +516,79 @@ stmg_status assemble_into(stmg_t h, const double* q, double* b) {
     CK(cudaMemcpyAsync(h->qstage, q, n * sizeof(double), cudaMemcpyDefault, h->s));
     qd = h->qstage;
   }
-  CK(launch_assemble_load(L.N, L.NT, L.pitch, L.dx, qd, b, h->s));
+  CK(launch_assemble_load(view<double>(L, h->o.omega), L.dx, qd, b, h->s));
   return STMG_OK;
 }
 
 // ||b - J u||^2 on level 0 in FP64 (u null: ||b||^2).
 stmg_status resnorm2(stmg_t h, bool adj, const double* u, const double* b, double* out) {
   Level& L = h->lev[0];
-  CK((launch_resnorm<double, double>(view<double>(L, h->o.omega), adj, u, b, nullptr, h->partials, h->scal,
-                                     h->s)));
+  CK(launch_resnorm<double>(view<double>(L, h->o.omega), adj, u, b, h->partials, h->scal, h->s));
   return read_scalar(h, h->scal, out);
 }
 
-// The solver loop of Sec. 3.1 on level 0's u and b (already in place).
+void reset_graphs(stmg_t h) {
+  for (auto& row : h->gexec)
+    for (auto& g : row)
+      if (g) {
+        cudaGraphExecDestroy(g);
+        g = nullptr;
+      }
+  h->graph_u0 = nullptr;
+}
+
+// Records what body() enqueues as a CUDA graph (captured on the handle's private stream;
+// the graph itself is launched on the handle's stream).
+template <typename F>
+stmg_status capture_graph(stmg_t h, cudaGraphExec_t* out, unsigned* nkernels, F body) {
+  cudaStream_t user = h->s;
+  const unsigned long long before = launches_so_far();
+  h->s = h->cs;
+  cudaError_t e = cudaStreamBeginCapture(h->cs, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    h->s = user;
+    return fail(h, STMG_ECUDA, "cudaStreamBeginCapture: %s", cudaGetErrorString(e));
+  }
+  stmg_status st = body();
+  *nkernels = (unsigned)(launches_so_far() - before);
+  count_launches(0u - *nkernels);  // capture only records; launches are counted per replay
+  cudaGraph_t g = nullptr;
+  e = cudaStreamEndCapture(h->cs, &g);
+  h->s = user;
+  if (st != STMG_OK) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return st;
+  }
+  if (e != cudaSuccess) return fail(h, STMG_ECUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(e));
+  e = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    *out = nullptr;
+    return fail(h, STMG_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+  }
+  return STMG_OK;
+}
+
+// The FP64 graphs were captured with level-0 u in one particular ping-pong buffer; a
+// solve starts by putting u back there (before anything is written to it).
+void normalize_level0(stmg_t h) {
+  Level& L = h->lev[0];
+  if (h->graph_u0 && L.u != h->graph_u0) std::swap(L.u, L.t);
+}
+
+// The solver loop of Sec. 3.1 on level 0's u and scaled b (already in place).
+//
+// FP64: the residual norm of the iterate u_n is accumulated by the first pre-smoothing
+// sweep of cycle n+1 (that sweep evaluates b - J u_n anyway); the termination test is
+// taken on it before the rest of that cycle runs, and if the solve stops, u_n is the
+// sweep's input, still intact in the other ping-pong buffer.
+// Mixed: r = b - J u in FP64 (also the scaled FP32 right-hand side), one FP32 V-cycle
+// from zero on J e = r, u += e.
 stmg_status solve_loop(stmg_t h, bool adj, bool warm, int* cycles_out, double* relres_out) {
   Level& L = h->lev[0];
   const stmg_opts& o = h->o;
+  const LevelView<double> lv = view<double>(L, o.omega);
   if (!warm) CK(cudaMemsetAsync(L.u, 0, L.nvec * sizeof(double), h->s));
   double nb2 = 0.0;
   CKS(resnorm2(h, adj, nullptr, L.b, &nb2));
@@ -422,28 +600,81 @@ stmg_status solve_loop(stmg_t h, bool adj, bool warm, int* cycles_out, double* r
     st = STMG_OK;
   } else if (!std::isfinite(nb2)) {
     return fail(h, STMG_EINVAL, "right-hand side contains NaN or Inf");
+  } else if (o.precision == STMG_MIXED) {
+    const double nb = std::sqrt(nb2);
+    double r2 = nb2;
+    CK(launch_defect(lv, adj, L.u, L.b, L.b32, h->partials, h->scal, h->s));
+    CKS(read_scalar(h, h->scal, &r2));
+    rel = std::sqrt(r2) / nb;
+    if (rel < o.tol) st = STMG_OK;
+    cudaGraphExec_t& gx = h->gexec[1][adj ? 1 : 0];
+    unsigned& gk = h->gkernels[1][adj ? 1 : 0];
+    for (int cyc = 1; cyc <= o.max_cycles && st != STMG_OK; ++cyc) {
+      if (!gx) {
+        CKS(capture_graph(h, &gx, &gk, [&]() -> stmg_status {
+          if (o.nu > 0) {
+            CKS(vcycle32_fused(h, 0, adj, L.u));
+          } else {
+            CKS(vcycle<float>(h, 0, adj, true, false));
+            CK(launch_add_correction(L.nvec, L.u, L.u32, h->s));
+          }
+          CK(launch_defect(lv, adj, L.u, L.b, L.b32, h->partials, h->scal, h->s));
+          return STMG_OK;
+        }));
+      }
+      CK(cudaGraphLaunch(gx, h->s));
+      count_launches(gk);
+      CKS(read_scalar(h, h->scal, &r2));
+      rel = std::sqrt(r2) / nb;
+      cycles = cyc;
+      if (!(rel <= o.div_tol)) {  // also catches NaN
+        st = STMG_EDIVERGED;
+        break;
+      }
+      if (rel < o.tol) st = STMG_OK;
+    }
   } else {
     const double nb = std::sqrt(nb2);
     double r2 = nb2;
-    if (o.precision == STMG_MIXED) {
-      CK(launch_defect(view<double>(L, o.omega), adj, L.u, L.b, L.b32, h->partials, h->scal, h->s));
-      CKS(read_scalar(h, h->scal, &r2));
+    const bool one_level = h->lev.size() == 1;
+    // the first sweep of cycle 1 (with the norm of the starting iterate if it is not 0)
+    if (!one_level && o.nu > 0) {
+      if (warm) {
+        CK(launch_sweep_norm<double>(lv, adj, L.u, L.b, L.t, h->partials, h->scal, h->s));
+        CKS(read_scalar(h, h->scal, &r2));
+      } else {
+        CK(cudaMemcpyAsync(L.t, L.b, L.nvec * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
+      }
     } else if (warm) {
       CKS(resnorm2(h, adj, L.u, L.b, &r2));
     }
     rel = std::sqrt(r2) / nb;
+    bool pending = !one_level && o.nu > 0;  // u -> t holds the first sweep of the next cycle
     if (rel < o.tol) st = STMG_OK;
+    cudaGraphExec_t& gx = h->gexec[0][adj ? 1 : 0];
+    unsigned& gk = h->gkernels[0][adj ? 1 : 0];
     for (int cyc = 1; cyc <= o.max_cycles && st != STMG_OK; ++cyc) {
-      if (o.precision == STMG_MIXED) {
-        CK(cudaMemsetAsync(L.u32, 0, L.nvec * sizeof(float), h->s));
-        CKS(vcycle<float>(h, 0, adj));
-        CK(launch_add_correction(L.nvec, L.u, L.u32, h->s));
-        CK(launch_defect(view<double>(L, o.omega), adj, L.u, L.b, L.b32, h->partials, h->scal, h->s));
-        CKS(read_scalar(h, h->scal, &r2));
+      if (pending) {
+        // one graph: the rest of this cycle and the first sweep of the next, whose
+        // norm is that of this cycle's result (2 nu buffer swaps on level 0: even)
+        if (!gx) {
+          double* u_before = L.u;
+          CKS(capture_graph(h, &gx, &gk, [&]() -> stmg_status {
+            std::swap(L.u, L.t);
+            CKS(vcycle<double>(h, 0, adj, false, true));
+            CK(launch_sweep_norm<double>(lv, adj, L.u, L.b, L.t, h->partials, h->scal, h->s));
+            return STMG_OK;
+          }));
+          if (L.u != u_before) return fail(h, STMG_ECUDA, "internal: odd number of level-0 swaps in a cycle");
+          h->graph_u0 = L.u;
+        }
+        CK(cudaGraphLaunch(gx, h->s));
+        count_launches(gk);
       } else {
-        CKS(vcycle<double>(h, 0, adj));
-        CKS(resnorm2(h, adj, L.u, L.b, &r2));
+        CKS(vcycle<double>(h, 0, adj, false, false));
+        CK(launch_resnorm<double>(lv, adj, L.u, L.b, h->partials, h->scal, h->s));
       }
+      CKS(read_scalar(h, h->scal, &r2));
       rel = std::sqrt(r2) / nb;
       cycles = cyc;
       if (!(rel <= o.div_tol)) {  // also catches NaN
@@ -486,6 +717,7 @@ stmg_status read_material(stmg_t h, int n, const double* k, const double* c, std
 }
 
 stmg_status build_hierarchy(stmg_t h, const std::vector<double>& hk, const std::vector<double>& hc) {
+  reset_graphs(h);
   std::vector<Level> nl = plan_levels(h->o, h->N, h->NT, h->L, h->tT, hk.data(), hc.data());
   // keep device buffers of levels whose shape is unchanged
   for (size_t l = 0; l < nl.size(); ++l) {
@@ -545,6 +777,8 @@ stmg_status stmg_create(stmg_t* out, int nel, int nt, double L, double t_end, co
   *out = nullptr;
   if (nel < 1 || nt < 1 || !finite_pos(L) || !finite_pos(t_end))
     return fail(nullptr, STMG_EINVAL, "need nel >= 1, nt >= 1, L > 0, t_end > 0");
+  if ((long long)(nel + 1) * (long long)(nt + 1) >= (1LL << 31))
+    return fail(nullptr, STMG_EINVAL, "grid too large: (nel+1)(nt+1) must stay below 2^31 DOFs");
   h = new (std::nothrow) stmg_handle();
   if (!h) return fail(nullptr, STMG_ENOMEM, "host allocation failed");
   if (opts) h->o = *opts;
@@ -560,6 +794,10 @@ stmg_status stmg_create(stmg_t* out, int nel, int nt, double L, double t_end, co
     cudaError_t e = cudaMallocHost((void**)&h->hscal, 8 * sizeof(double));
     if (e != cudaSuccess) st = fail(h, STMG_ENOMEM, "cudaMallocHost failed: %s", cudaGetErrorString(e));
   }
+  if (st == STMG_OK) {
+    cudaError_t e = cudaStreamCreateWithFlags(&h->cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) st = fail(h, STMG_ECUDA, "cudaStreamCreateWithFlags: %s", cudaGetErrorString(e));
+  }
   if (st == STMG_OK) st = build_hierarchy(h, hk, hc);
   if (st != STMG_OK) {
     g_global_error = h->err;
@@ -574,6 +812,8 @@ void stmg_destroy(stmg_t h) {
   if (!h) return;
   if (h->s) cudaStreamSynchronize(h->s);
   else cudaDeviceSynchronize();
+  reset_graphs(h);
+  if (h->cs) cudaStreamDestroy(h->cs);
   for (Level& L : h->lev) free_level(L);
   dfree(h->partials);
   dfree(h->scal);
@@ -606,6 +846,7 @@ stmg_status stmg_assemble_load(stmg_t h, const double* q_el, double* b) {
   if (!q_el || !b) return fail(h, STMG_EINVAL, "NULL array");
   Level& L = h->lev[0];
   CKS(assemble_into(h, q_el, L.t));
+  CK(launch_scale<double>(view<double>(L, h->o.omega), false, L.t, h->s));
   CKS(copy_out(h, b, L.t, L.pitch, L.NT + 1, L.N + 1));
   CK(cudaStreamSynchronize(h->s));
   return STMG_OK;
@@ -617,8 +858,13 @@ static stmg_status solve_common(stmg_t h, bool adj, const double* q_el, const do
   if (!u || ((q_el == nullptr) == (b_nodal == nullptr)))
     return fail(h, STMG_EINVAL, "need u and exactly one of q_el / b_nodal");
   Level& L = h->lev[0];
-  if (q_el) CKS(assemble_into(h, q_el, L.b));
-  else CKS(copy_in(h, L.b, L.pitch, b_nodal, L.NT + 1, L.N + 1));
+  normalize_level0(h);
+  if (q_el) {
+    CKS(assemble_into(h, q_el, L.b));
+  } else {
+    CKS(copy_in(h, L.b, L.pitch, b_nodal, L.NT + 1, L.N + 1));
+    CK(launch_scale<double>(view<double>(L, h->o.omega), true, L.b, h->s));
+  }
   if (warm) CKS(copy_in(h, L.u, L.pitch, u, L.NT + 1, L.N + 1));
   stmg_status st = solve_loop(h, adj, warm != 0, cycles, relres);
   if (st != STMG_OK && st != STMG_EDIVERGED && st != STMG_EMAXITER) return st;
@@ -719,6 +965,7 @@ stmg_status stmg_smooth(stmg_t h, int level, int adjoint, int nsweeps, double* u
   CKS(ensure_fp64(h, L));
   CKS(copy_in(h, L.u, L.pitch, u, L.NT + 1, L.N + 1));
   CKS(copy_in(h, L.b, L.pitch, b, L.NT + 1, L.N + 1));
+  CK(launch_scale<double>(view<double>(L, h->o.omega), true, L.b, h->s));
   CKS(smooth_level<double>(h, L, adjoint != 0, nsweeps));
   CKS(copy_out(h, u, L.u, L.pitch, L.NT + 1, L.N + 1));
   CK(cudaStreamSynchronize(h->s));
@@ -734,7 +981,8 @@ stmg_status stmg_restrict(stmg_t h, int level, const double* r, double* bc) {
   CKS(ensure_fp64(h, L));
   CKS(ensure_fp64(h, C));
   CKS(copy_in(h, L.t, L.pitch, r, L.NT + 1, L.N + 1));
-  CK(launch_restrict<double>(L.next, L.N, L.NT, L.pitch, L.t, C.N, C.NT, C.pitch, C.b, h->s));
+  CK(launch_restrict<double>(L.next, L.N, L.NT, L.pitch, L.t, view<double>(C, h->o.omega), C.b, h->s));
+  CK(launch_scale<double>(view<double>(C, h->o.omega), false, C.b, h->s));
   CKS(copy_out(h, bc, C.b, C.pitch, C.NT + 1, C.N + 1));
   CK(cudaStreamSynchronize(h->s));
   return STMG_OK;
@@ -763,8 +1011,72 @@ stmg_status stmg_exact_solve(stmg_t h, int level, int adjoint, const double* b, 
   if ((size_t)(L.N + 2) * 16 > 200 * 1024) return fail(h, STMG_EINVAL, "level too wide for the exact solver");
   CKS(ensure_fp64(h, L));
   CKS(copy_in(h, L.b, L.pitch, b, L.NT + 1, L.N + 1));
-  CK(launch_exact<double>(thomas_view(L), adjoint != 0, L.b, L.u, h->s));
+  CK(launch_scale<double>(view<double>(L, h->o.omega), true, L.b, h->s));
+  CK(launch_exact<double>(thomas_view(L, h->o.omega), adjoint != 0, L.b, L.u, h->s));
   CKS(copy_out(h, u, L.u, L.pitch, L.NT + 1, L.N + 1));
+  CK(cudaStreamSynchronize(h->s));
+  return STMG_OK;
+}
+
+static stmg_status slabs_common(stmg_t h, const double* b_nodal, const double* ckpt, int slab_rows,
+                                const double** ckpt_dev) {
+  if (!b_nodal || !ckpt || slab_rows < 1) return fail(h, STMG_EINVAL, "need b_nodal, ckpt and slab_rows >= 1");
+  Level& L = h->lev[0];
+  if ((L.N + 511) / 512 > kMaxNodesPerThread) return fail(h, STMG_EINVAL, "nel too large for the slab solver");
+  normalize_level0(h);
+  CKS(copy_in(h, L.b, L.pitch, b_nodal, L.NT + 1, L.N + 1));
+  CK(launch_scale<double>(view<double>(L, h->o.omega), true, L.b, h->s));
+  const int nslabs = (L.NT + slab_rows - 1) / slab_rows;
+  const size_t n = (size_t)nslabs * (L.N + 1);
+  *ckpt_dev = ckpt;
+  if (!is_device_ptr(ckpt)) {
+    if (h->qstage_n < n) {
+      dfree(h->qstage);
+      h->qstage_n = 0;
+      CKS(dalloc(h, &h->qstage, std::max(n, (size_t)(L.NT + 1) * L.N)));
+      h->qstage_n = std::max(n, (size_t)(L.NT + 1) * L.N);
+    }
+    CK(cudaMemcpyAsync(h->qstage, ckpt, n * sizeof(double), cudaMemcpyDefault, h->s));
+    *ckpt_dev = h->qstage;
+  }
+  return STMG_OK;
+}
+
+stmg_status stmg_recompute_slabs(stmg_t h, const double* b_nodal, const double* ckpt, int slab_rows, double* u) {
+  if (!h) return fail(nullptr, STMG_EINVAL, "NULL handle");
+  if (!u) return fail(h, STMG_EINVAL, "NULL u");
+  const double* cd = nullptr;
+  CKS(slabs_common(h, b_nodal, ckpt, slab_rows, &cd));
+  Level& L = h->lev[0];
+  CK(launch_slabs(slab_view(L, h->o.omega, slab_rows), L.b, cd, L.u, nullptr, nullptr, h->s));
+  CKS(copy_out(h, u, L.u, L.pitch, L.NT + 1, L.N + 1));
+  CK(cudaStreamSynchronize(h->s));
+  return STMG_OK;
+}
+
+stmg_status stmg_sensitivity_slabs(stmg_t h, const double* chi, const double* simp6, const double* b_nodal,
+                                   const double* ckpt, int slab_rows, const double* lam, double* g) {
+  if (!h) return fail(nullptr, STMG_EINVAL, "NULL handle");
+  if (!chi || !simp6 || !lam || !g) return fail(h, STMG_EINVAL, "NULL array");
+  const double* cd = nullptr;
+  CKS(slabs_common(h, b_nodal, ckpt, slab_rows, &cd));
+  Level& L = h->lev[0];
+  const int nslabs = (L.NT + slab_rows - 1) / slab_rows;
+  const size_t need = 2 * (size_t)nslabs * L.N;
+  if (h->sens_n < need) {
+    dfree(h->sens);
+    h->sens_n = 0;
+    CKS(dalloc(h, &h->sens, need));
+    h->sens_n = need;
+  }
+  if (!h->gstage) CKS(dalloc(h, &h->gstage, 2 * (size_t)L.N));
+  CKS(copy_in(h, L.t, L.pitch, lam, L.NT + 1, L.N + 1));
+  CK(cudaMemcpyAsync(h->gstage, chi, L.N * sizeof(double), cudaMemcpyDefault, h->s));
+  CK(launch_slabs(slab_view(L, h->o.omega, slab_rows), L.b, cd, nullptr, L.t, h->sens, h->s));
+  Simp6 sp;
+  for (int i = 0; i < 6; ++i) sp.v[i] = simp6[i];
+  CK(launch_sens_final(L.N, nslabs, h->gstage, sp, h->sens, h->gstage + L.N, h->s));
+  CK(cudaMemcpyAsync(g, h->gstage + L.N, L.N * sizeof(double), cudaMemcpyDefault, h->s));
   CK(cudaStreamSynchronize(h->s));
   return STMG_OK;
 }
@@ -775,13 +1087,17 @@ stmg_status stmg_vcycle(stmg_t h, int adjoint, double* u, const double* b) {
   Level& L = h->lev[0];
   CKS(copy_in(h, L.u, L.pitch, u, L.NT + 1, L.N + 1));
   CKS(copy_in(h, L.b, L.pitch, b, L.NT + 1, L.N + 1));
+  CK(launch_scale<double>(view<double>(L, h->o.omega), true, L.b, h->s));
   if (h->o.precision == STMG_MIXED) {
     CK(launch_defect(view<double>(L, h->o.omega), adjoint != 0, L.u, L.b, L.b32, h->partials, h->scal, h->s));
-    CK(cudaMemsetAsync(L.u32, 0, L.nvec * sizeof(float), h->s));
-    CKS(vcycle<float>(h, 0, adjoint != 0));
-    CK(launch_add_correction(L.nvec, L.u, L.u32, h->s));
+    if (h->o.nu > 0) {
+      CKS(vcycle32_fused(h, 0, adjoint != 0, L.u));
+    } else {
+      CKS(vcycle<float>(h, 0, adjoint != 0, true, false));
+      CK(launch_add_correction(L.nvec, L.u, L.u32, h->s));
+    }
   } else {
-    CKS(vcycle<double>(h, 0, adjoint != 0));
+    CKS(vcycle<double>(h, 0, adjoint != 0, false, false));
   }
   CKS(copy_out(h, u, L.u, L.pitch, L.NT + 1, L.N + 1));
   CK(cudaStreamSynchronize(h->s));

@@ -3,17 +3,26 @@
 // Device layout of one level with N elements and NT steps: a space-time vector is
 // (NT+1) rows of `pitch` values; columns 0..N hold the nodes, columns N+1..pitch-1 are
 // zero padding that no kernel ever writes (pitch >= N+2, so the right neighbour of node
-// N is always a zero padding value).  The stencil coefficients of a level are 8 arrays of
-// `pitch` values each (struct of arrays, see CoefSlot), built once per level:
+// N is always a zero padding value).
+//
+// Operator (Sec. 2.2 stencil with the Dirichlet treatment of Appendix A): for the
+// non-Dirichlet DOFs (n >= 1, i >= 1)
 //
 //   (J u)[n][i] = L_i u[n][i-1] + D_i u[n][i] + U_i u[n][i+1]
-//               + PL_i u[p][i-1] + PC_i u[p][i] + PR_i u[p][i+1]
+//               + PL_i u[p][i-1] + PC_i u[p][i] + PR_i u[p][i+1],
 //
-// for the non-Dirichlet DOFs (n >= 1, i >= 1), where p = n-1 for J (present for n >= 2)
-// and p = n+1 for J^T (present for n <= NT-1); the mass and stiffness blocks are
-// symmetric, so J and J^T share the coefficients (Sec. 2.2, Sec. 7.2).  Dirichlet DOFs
-// (row 0 and column 0) have (J u) = W_Diri u (Appendix A).  L_1 = PL_1 = 0 and
-// U_N = PR_N = 0 remove the Dirichlet column and the missing element past x = L.
+// p = n-1 for J (present for n >= 2) and p = n+1 for J^T (present for n <= NT-1); the
+// mass and stiffness blocks are symmetric, so J and J^T share the coefficients (Sec. 7.2).
+// Dirichlet DOFs (row 0 and column 0) have (J u) = W u.  L_1 = PL_1 = 0 and
+// U_N = PR_N = 0 remove the eliminated column 0 and the missing element past x = L.
+//
+// Scaled form used by the smoother (Sec. 3.1 damped Jacobi with D the diagonal of J):
+// every level stores its right-hand side as b' = (omega / D) b, and the coefficients
+// S_k = -omega c_k / D for the five off-diagonal neighbours, so that one sweep is
+//
+//   u <- (1 - omega) u + b' + sum_k S_k u_k          (6 fused multiply-adds),
+//
+// and the residual is r = b - J u = (D / omega) (b' - omega u + sum_k S_k u_k).
 #pragma once
 #include <cstddef>
 #include <cstdint>
@@ -22,7 +31,13 @@
 
 namespace stmg {
 
-enum CoefSlot { kL = 0, kD = 1, kU = 2, kPL = 3, kPC = 4, kPR = 5, kInvD = 6, kNumCoef = 8 };
+enum CoefSlot {
+  kL = 0, kD = 1, kU = 2, kPL = 3, kPC = 4, kPR = 5,  // J entries
+  kW = 6,                                             // omega / D (b -> b')
+  kDW = 7,                                            // D / omega (b' -> b)
+  kSL = 8, kSU = 9, kSPL = 10, kSPC = 11, kSPR = 12,  // -omega c_k / D
+  kNumCoef = 16
+};
 
 inline int level_pitch(int N) {
   int need = N + 2;
@@ -30,17 +45,34 @@ inline int level_pitch(int N) {
   return (need + align - 1) / align * align;
 }
 
-// Geometry of a level as the kernels see it.
+// x / d for 0 <= x < 2^31 by a multiply-high (Granlund & Montgomery 1994, round-up
+// variant): s = ceil(log2 d), M = floor(2^32 (2^s - d) / d) + 1, q = (mulhi(x, M) + x) >> s.
+struct FastDiv {
+  uint32_t d, M, s;
+};
+inline FastDiv make_fastdiv(uint32_t d) {
+  uint32_t s = 0;
+  while ((1ull << s) < d) ++s;
+  const uint64_t M = ((1ull << 32) * ((1ull << s) - d)) / d + 1;
+  return FastDiv{d, (uint32_t)M, s};
+}
+
+// Geometry and coefficients of a level as the kernels see it.
 template <typename T>
 struct LevelView {
   int N, NT, pitch;
+  FastDiv fd;     // division by N + 1
   const T* coef;  // kNumCoef * pitch
   T W;            // W_Diri
+  T omega;
+  T omc;          // 1 - omega
   T wW;           // omega / W_Diri
+  T Wo;           // W_Diri / omega
 };
 
 // Precomputed Thomas factors of the interior tridiagonal block (M/dt + K)_int and the
-// mass coupling, FP64, arrays of N+1 values indexed by node (entry 0 unused).
+// mass coupling, FP64, arrays of N+2 values indexed by node (entry 0 unused), plus
+// D / omega per node to turn the stored b' back into b.
 struct ThomasView {
   int N, NT, pitch;
   const double* lo;   // sub-diagonal coefficient (of node i-1)
@@ -49,7 +81,8 @@ struct ThomasView {
   const double* pl;   // time-coupling coefficients PL, PC, PR (negated mass / dt)
   const double* pc;
   const double* pr;
-  double W;
+  const double* dw;   // D_i / omega
+  double W, omega;
 };
 
 // Sets the message returned by stmg_last_error(NULL) on this host thread.
@@ -59,31 +92,44 @@ void set_global_error(const char* msg);
 void count_launches(unsigned n);
 unsigned long long launches_so_far();
 
+constexpr int kNormBlocks = 608;  // 4 x 152 SMs: fixed grid of every reduction
+
 // ---- launchers (stmg_kernels.cu); all return cudaGetLastError() after the launch ----
+// One damped-Jacobi sweep uo <- u + omega D^-1 (b - J u) with b' = (omega/D) b stored.
 template <typename T>
-cudaError_t launch_jacobi(const LevelView<T>& lv, bool adj, const T* u, const T* b, T* uo, cudaStream_t s);
+cudaError_t launch_sweep(const LevelView<T>& lv, bool adj, const T* u, const T* bs, T* uo, cudaStream_t s);
+// The same sweep, also writing the partial sums of ||b - J u||^2 (u = the input iterate)
+// into partials[kNormBlocks]; then out[0] = the total.  Deterministic.
 template <typename T>
-cudaError_t launch_residual(const LevelView<T>& lv, bool adj, const T* u, const T* b, T* r, cudaStream_t s);
-// y = J u
+cudaError_t launch_sweep_norm(const LevelView<T>& lv, bool adj, const T* u, const T* bs, T* uo, double* partials,
+                              double* out, cudaStream_t s);
+// r = b - J u from the stored b'.
+template <typename T>
+cudaError_t launch_residual(const LevelView<T>& lv, bool adj, const T* u, const T* bs, T* r, cudaStream_t s);
+// y = J u (plain coefficients).
 template <typename T>
 cudaError_t launch_apply(const LevelView<T>& lv, bool adj, const T* u, T* y, cudaStream_t s);
+// b'_c = (omega / D_c) (s P^T r): restriction with the coarse scaling folded in.
 template <typename T>
-cudaError_t launch_restrict(int type, int Nf, int NTf, int pf, const T* r, int Nc, int NTc, int pc, T* bc,
+cudaError_t launch_restrict(int type, int Nf, int NTf, int pf, const T* r, const LevelView<T>& cv, T* bc,
                             cudaStream_t s);
 template <typename T>
 cudaError_t launch_prolong_add(int type, int Nf, int NTf, int pf, T* u, int Nc, int NTc, int pc, const T* z,
                                cudaStream_t s);
+// Exact solve of J u = b from the stored b'.
 template <typename T>
-cudaError_t launch_exact(const ThomasView& tv, bool adj, const T* b, T* u, cudaStream_t s);
+cudaError_t launch_exact(const ThomasView& tv, bool adj, const T* bs, T* u, cudaStream_t s);
+// x <- (omega/D) x (to_scaled) or (D/omega) x over a level vector, in place.
+template <typename T>
+cudaError_t launch_scale(const LevelView<T>& lv, bool to_scaled, T* x, cudaStream_t s);
 
-// Sum of squares of (b - J u) over all DOFs (u == nullptr: of b) into partials[kNormBlocks];
-// then a single-block pass writes the total to out[0].  Deterministic (fixed order).
-constexpr int kNormBlocks = 608;  // 4 x 152 SMs
-template <typename T, typename R>
-cudaError_t launch_resnorm(const LevelView<T>& lv, bool adj, const T* u, const T* b, R* r_out, double* partials,
-                           double* out, cudaStream_t s);
-// FP64 residual for the mixed scheme: r32 = float(b - J u), with its squared norm.
-cudaError_t launch_defect(const LevelView<double>& lv, bool adj, const double* u, const double* b, float* r32,
+// ||b - J u||^2 (u == nullptr: ||b||^2) from the stored b' into out[0].
+template <typename T>
+cudaError_t launch_resnorm(const LevelView<T>& lv, bool adj, const T* u, const T* bs, double* partials, double* out,
+                           cudaStream_t s);
+// Mixed scheme, FP64 level 0: y = (omega/D)(b - J u) stored as FP32 (it is the scaled
+// right-hand side of the FP32 cycle), with ||b - J u||^2 into out[0].
+cudaError_t launch_defect(const LevelView<double>& lv, bool adj, const double* u, const double* bs, float* ys32,
                           double* partials, double* out, cudaStream_t s);
 // u64 += double(e32) over the whole padded array.
 cudaError_t launch_add_correction(size_t n, double* u, const float* e, cudaStream_t s);
@@ -98,13 +144,16 @@ struct Simp6 {
   double v[6];
 };
 cudaError_t launch_simp(int N, const double* chi, Simp6 sp, double* k, double* c, cudaStream_t s);
-// Nodal load from element loads q[(NT+1) x N] (dense) into b (padded layout).
-cudaError_t launch_assemble_load(int N, int NT, int pitch, double dx, const double* q, double* b, cudaStream_t s);
+// b' = (omega/D) B b_Neu from element loads q[(NT+1) x N] (dense) into the padded layout.
+cudaError_t launch_assemble_load(const LevelView<double>& lv, double dx, const double* q, double* bs, cudaStream_t s);
 // Sensitivity: partial sums over time chunks, then the per-element reduction.
 constexpr int kSensRowsPerChunk = 256;
 // scratch: 2 * sens_chunks(NT) * N doubles.
 cudaError_t launch_sensitivity(int N, int NT, int pitch, double dx, double dt, const double* chi, Simp6 sp,
                                const double* u, const double* lam, double* scratch, double* g, cudaStream_t s);
+// Per-element reduction of scratch[2 * chunks * N] partial sums into the gradient.
+cudaError_t launch_sens_final(int N, int chunks, const double* chi, Simp6 sp, const double* scratch, double* g,
+                              cudaStream_t s);
 // Time levels 0..NT in chunks of kSensRowsPerChunk rows.
 inline int sens_chunks(int NT) { return (NT + kSensRowsPerChunk) / kSensRowsPerChunk; }
 

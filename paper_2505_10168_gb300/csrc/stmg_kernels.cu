@@ -25,6 +25,13 @@ inline unsigned blocks_for(long long n, int threads = kThreads) {
   return (unsigned)(b < 1 ? 1 : b);
 }
 
+// Row and node of a flat DOF index idx = n (N+1) + i (idx < 2^31).
+__device__ __forceinline__ void split_index(uint32_t idx, const FastDiv& fd, int& n, int& i) {
+  const uint32_t q = (uint32_t)(((uint64_t)__umulhi(idx, fd.M) + idx) >> fd.s);
+  n = (int)q;
+  i = (int)(idx - q * fd.d);
+}
+
 // (J u) at DOF (n, i) of a level, p = n * pitch + i (Sec. 2.2 stencil, Appendix A).
 template <typename T>
 __device__ __forceinline__ T apply_at(const LevelView<T>& lv, bool adj, const T* __restrict__ u, int n, int i,
@@ -45,118 +52,50 @@ __device__ __forceinline__ T apply_at(const LevelView<T>& lv, bool adj, const T*
   return acc;
 }
 
-// Damped Jacobi step (Sec. 3.1): uo = u + omega D^-1 (b - J u), D^-1 omega stored per node.
+// acc + sum_k S_k u_k over the off-diagonal neighbours of a non-Dirichlet DOF.
 template <typename T, bool ADJ>
-__global__ void __launch_bounds__(kThreads) k_jacobi(LevelView<T> lv, const T* __restrict__ u,
-                                                     const T* __restrict__ b, T* __restrict__ uo) {
-  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  const long long total = (long long)(lv.NT + 1) * (lv.N + 1);
+__device__ __forceinline__ T add_neighbours(const LevelView<T>& lv, const T* __restrict__ u, int n, int i, size_t p,
+                                            T acc) {
+  const T* cf = lv.coef;
+  const int P = lv.pitch;
+  acc = fma(cf[kSL * P + i], u[p - 1], acc);
+  acc = fma(cf[kSU * P + i], u[p + 1], acc);
+  const bool has_prev = ADJ ? (n < lv.NT) : (n > 1);
+  if (has_prev) {
+    const size_t q = ADJ ? p + P : p - P;
+    acc = fma(cf[kSPL * P + i], u[q - 1], acc);
+    acc = fma(cf[kSPC * P + i], u[q], acc);
+    acc = fma(cf[kSPR * P + i], u[q + 1], acc);
+  }
+  return acc;
+}
+
+// Damped Jacobi (Sec. 3.1) in the scaled form: uo = (1 - omega) u + b' + sum_k S_k u_k.
+template <typename T, bool ADJ>
+__global__ void __launch_bounds__(kThreads) k_sweep(LevelView<T> lv, uint32_t total, const T* __restrict__ u,
+                                                    const T* __restrict__ bs, T* __restrict__ uo) {
+  const uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= total) return;
-  const int n = (int)(idx / (lv.N + 1));
-  const int i = (int)(idx - (long long)n * (lv.N + 1));
+  int n, i;
+  split_index(idx, lv.fd, n, i);
   const size_t p = (size_t)n * lv.pitch + i;
-  const T r = b[p] - apply_at(lv, ADJ, u, n, i, p);
-  const T w = (n == 0 || i == 0) ? lv.wW : lv.coef[kInvD * lv.pitch + i];
-  uo[p] = fma(w, r, u[p]);
+  T acc = fma(lv.omc, u[p], bs[p]);
+  if (n != 0 && i != 0) acc = add_neighbours<T, ADJ>(lv, u, n, i, p, acc);
+  uo[p] = acc;
 }
 
-// r = b - J u (MODE 0) or y = J u (MODE 1).
-template <typename T, bool ADJ, int MODE>
-__global__ void __launch_bounds__(kThreads) k_residual(LevelView<T> lv, const T* __restrict__ u,
-                                                       const T* __restrict__ b, T* __restrict__ r) {
-  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  const long long total = (long long)(lv.NT + 1) * (lv.N + 1);
-  if (idx >= total) return;
-  const int n = (int)(idx / (lv.N + 1));
-  const int i = (int)(idx - (long long)n * (lv.N + 1));
-  const size_t p = (size_t)n * lv.pitch + i;
-  const T ju = apply_at(lv, ADJ, u, n, i, p);
-  r[p] = MODE == 0 ? b[p] - ju : ju;
+// Scaled residual y = b' - omega u + sum_k S_k u_k = (omega / D)(b - J u).
+template <typename T, bool ADJ>
+__device__ __forceinline__ T scaled_residual(const LevelView<T>& lv, const T* __restrict__ u,
+                                             const T* __restrict__ bs, int n, int i, size_t p) {
+  T y = fma(-lv.omega, u[p], bs[p]);
+  if (n != 0 && i != 0) y = add_neighbours<T, ADJ>(lv, u, n, i, p, y);
+  return y;
 }
 
-// Restriction b_c = s P^T r (Sec. 3.1): x: 1/2 [1 2 1] within the row, s = 1;
-// t (causal): rows 2m and 2m+1, s = 1/2 (row 2m+1 absent past the last fine row).
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_restrict(int type, int Nf, int NTf, int pf, const T* __restrict__ r,
-                                                       int Nc, int NTc, int pc, T* __restrict__ bc) {
-  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  const long long total = (long long)(NTc + 1) * (Nc + 1);
-  if (idx >= total) return;
-  const int m = (int)(idx / (Nc + 1));
-  const int j = (int)(idx - (long long)m * (Nc + 1));
-  T acc;
-  if (type == 1) {
-    const T* row = r + (size_t)m * pf;
-    acc = row[2 * j];
-    if (2 * j - 1 >= 0) acc += T(0.5) * row[2 * j - 1];
-    if (2 * j + 1 <= Nf) acc += T(0.5) * row[2 * j + 1];
-  } else {
-    acc = r[(size_t)(2 * m) * pf + j];
-    if (2 * m + 1 <= NTf) acc += r[(size_t)(2 * m + 1) * pf + j];
-    acc *= T(0.5);
-  }
-  bc[(size_t)m * pc + j] = acc;
-}
-
-// u += P z (Sec. 3.1): x: fine node 2j gets z_j, node 2j+1 gets (z_j + z_{j+1}) / 2;
-// t (causal): fine rows 2m and 2m+1 get coarse row m.
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_prolong_add(int type, int Nf, int NTf, int pf, T* __restrict__ u,
-                                                          int Nc, int NTc, int pc, const T* __restrict__ z) {
-  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  const long long total = (long long)(NTf + 1) * (Nf + 1);
-  if (idx >= total) return;
-  const int n = (int)(idx / (Nf + 1));
-  const int i = (int)(idx - (long long)n * (Nf + 1));
-  T add;
-  if (type == 1) {
-    const T* zr = z + (size_t)n * pc;
-    add = (i & 1) ? T(0.5) * (zr[i >> 1] + zr[(i >> 1) + 1]) : zr[i >> 1];
-  } else {
-    add = z[(size_t)(n >> 1) * pc + i];
-  }
-  u[(size_t)n * pf + i] += add;
-}
-
-// Exact solve of J u = b (or J^T u = b) by implicit time stepping: Dirichlet DOFs
-// u = b / W; then for each step a Thomas solve of (M/dt + K)_int T_n = f_n with
-// f_n = b_n - (coupling to the previous step), forward in time for J and backward for
-// J^T.  Arithmetic in FP64 whatever the storage type.  One block; thread 0 runs the
-// sequential recurrence, the other threads fill the Dirichlet DOFs.
-template <typename T>
-__global__ void k_exact(ThomasView tv, bool adj, const T* __restrict__ b, T* __restrict__ u) {
-  extern __shared__ double sm[];
-  const int N = tv.N, NT = tv.NT, P = tv.pitch;
-  for (int i = threadIdx.x; i <= N; i += blockDim.x) u[i] = (T)((double)b[i] / tv.W);
-  for (int n = 1 + threadIdx.x; n <= NT; n += blockDim.x) u[(size_t)n * P] = (T)((double)b[(size_t)n * P] / tv.W);
-  __syncthreads();
-  if (threadIdx.x != 0) return;
-  // FP64 rows: prev (previous step, node 0 = 0 since its column is eliminated) and cur.
-  double* prev = sm;
-  double* cur = sm + (N + 2);
-  for (int i = 0; i <= N + 1; ++i) prev[i] = 0.0;
-  cur[0] = 0.0;
-  cur[N + 1] = 0.0;
-  for (int step = 1; step <= NT; ++step) {
-    const int n = adj ? NT + 1 - step : step;
-    const bool has_prev = adj ? (n < NT) : (n > 1);
-    const T* bn = b + (size_t)n * P;
-    // forward elimination (cur holds the modified right-hand side)
-    double dp = 0.0;
-    for (int i = 1; i <= N; ++i) {
-      double f = (double)bn[i];
-      if (has_prev) f -= tv.pl[i] * prev[i - 1] + tv.pc[i] * prev[i] + tv.pr[i] * prev[i + 1];
-      dp = (f - tv.lo[i] * dp) * tv.inv[i];
-      cur[i] = dp;
-    }
-    // back substitution
-    for (int i = N - 1; i >= 1; --i) cur[i] = cur[i] - tv.cp[i] * cur[i + 1];
-    T* un = u + (size_t)n * P;
-    for (int i = 1; i <= N; ++i) {
-      un[i] = (T)cur[i];
-      prev[i] = cur[i];
-    }
-  }
+__device__ __forceinline__ T unscale(const LevelView<T>& lv, int n, int i) {
+  return (n == 0 || i == 0) ? lv.Wo : lv.coef[kDW * lv.pitch + i];
 }
 
 // Block-level deterministic sum of one double per thread; result valid in thread 0.
@@ -173,21 +112,155 @@ __device__ __forceinline__ double block_sum(double v) {
   return red[0];
 }
 
-// Squared norm of r = b - J u (u null: r = b), optionally storing r as R.
-template <typename T, typename R, bool ADJ>
-__global__ void __launch_bounds__(kThreads) k_resnorm(LevelView<T> lv, const T* __restrict__ u,
-                                                      const T* __restrict__ b, R* __restrict__ r_out,
-                                                      double* __restrict__ partials) {
-  const long long total = (long long)(lv.NT + 1) * (lv.N + 1);
+// Sweep that also accumulates ||b - J u||^2 of the input iterate (fixed grid, grid-stride).
+template <typename T, bool ADJ>
+__global__ void __launch_bounds__(kThreads) k_sweep_norm(LevelView<T> lv, uint32_t total, const T* __restrict__ u,
+                                                         const T* __restrict__ bs, T* __restrict__ uo,
+                                                         double* __restrict__ partials) {
   double acc = 0.0;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const int n = (int)(idx / (lv.N + 1));
-    const int i = (int)(idx - (long long)n * (lv.N + 1));
+  for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+    int n, i;
+    split_index(idx, lv.fd, n, i);
     const size_t p = (size_t)n * lv.pitch + i;
-    const T r = u ? b[p] - apply_at(lv, ADJ, u, n, i, p) : b[p];
-    if (r_out) r_out[p] = (R)r;
-    acc = fma((double)r, (double)r, acc);
+    const T y = scaled_residual<T, ADJ>(lv, u, bs, n, i, p);
+    uo[p] = u[p] + y;
+    const double r = (double)(unscale(lv, n, i) * y);
+    acc = fma(r, r, acc);
+  }
+  const double s = block_sum<kThreads>(acc);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+// r = b - J u (MODE 0, from b') or y = J u (MODE 1, plain coefficients).
+template <typename T, bool ADJ, int MODE>
+__global__ void __launch_bounds__(kThreads) k_residual(LevelView<T> lv, uint32_t total, const T* __restrict__ u,
+                                                       const T* __restrict__ bs, T* __restrict__ r) {
+  const uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  int n, i;
+  split_index(idx, lv.fd, n, i);
+  const size_t p = (size_t)n * lv.pitch + i;
+  if (MODE == 0) r[p] = unscale(lv, n, i) * scaled_residual<T, ADJ>(lv, u, bs, n, i, p);
+  else r[p] = apply_at(lv, ADJ, u, n, i, p);
+}
+
+// Restriction b_c = s P^T r (Sec. 3.1), stored scaled by omega / D_c of the coarse level:
+// x: 1/2 [1 2 1] within the row, s = 1; t (causal): rows 2m and 2m+1, s = 1/2 (row 2m+1
+// absent past the last fine row).
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_restrict(int type, int Nf, int NTf, int pf, const T* __restrict__ r,
+                                                       LevelView<T> cv, uint32_t total, T* __restrict__ bc) {
+  const uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  int m, j;
+  split_index(idx, cv.fd, m, j);
+  T acc;
+  if (type == 1) {
+    const T* row = r + (size_t)m * pf;
+    acc = row[2 * j];
+    if (2 * j - 1 >= 0) acc += T(0.5) * row[2 * j - 1];
+    if (2 * j + 1 <= Nf) acc += T(0.5) * row[2 * j + 1];
+  } else {
+    acc = r[(size_t)(2 * m) * pf + j];
+    if (2 * m + 1 <= NTf) acc += r[(size_t)(2 * m + 1) * pf + j];
+    acc *= T(0.5);
+  }
+  const T sc = (m == 0 || j == 0) ? cv.wW : cv.coef[kW * cv.pitch + j];
+  bc[(size_t)m * cv.pitch + j] = sc * acc;
+}
+
+// u += P z (Sec. 3.1): x: fine node 2j gets z_j, node 2j+1 gets (z_j + z_{j+1}) / 2;
+// t (causal): fine rows 2m and 2m+1 get coarse row m.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_prolong_add(int type, FastDiv fdf, uint32_t total, int pf,
+                                                          T* __restrict__ u, int pc, const T* __restrict__ z) {
+  const uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  int n, i;
+  split_index(idx, fdf, n, i);
+  T add;
+  if (type == 1) {
+    const T* zr = z + (size_t)n * pc;
+    add = (i & 1) ? T(0.5) * (zr[i >> 1] + zr[(i >> 1) + 1]) : zr[i >> 1];
+  } else {
+    add = z[(size_t)(n >> 1) * pc + i];
+  }
+  u[(size_t)n * pf + i] += add;
+}
+
+// x <- (omega/D) x or (D/omega) x at every DOF (padding untouched).
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_scale(LevelView<T> lv, uint32_t total, bool to_scaled,
+                                                    T* __restrict__ x) {
+  const uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  int n, i;
+  split_index(idx, lv.fd, n, i);
+  const bool dir = n == 0 || i == 0;
+  const T f = to_scaled ? (dir ? lv.wW : lv.coef[kW * lv.pitch + i]) : (dir ? lv.Wo : lv.coef[kDW * lv.pitch + i]);
+  const size_t p = (size_t)n * lv.pitch + i;
+  x[p] = f * x[p];
+}
+
+// Exact solve of J u = b (or J^T u = b) by implicit time stepping: Dirichlet DOFs
+// u = b / W; then for each step a Thomas solve of (M/dt + K)_int T_n = f_n with
+// f_n = b_n - (coupling to the previous step), forward in time for J and backward for
+// J^T.  Arithmetic in FP64 whatever the storage type.  One block; thread 0 runs the
+// sequential recurrence, the other threads fill the Dirichlet DOFs.
+// The right-hand side arrives scaled (b' = (omega/D) b): b = (D/omega) b' in the interior
+// and u = b / W = b' / omega on the Dirichlet DOFs.
+template <typename T>
+__global__ void k_exact(ThomasView tv, bool adj, const T* __restrict__ b, T* __restrict__ u) {
+  extern __shared__ double sm[];
+  const int N = tv.N, NT = tv.NT, P = tv.pitch;
+  for (int i = threadIdx.x; i <= N; i += blockDim.x) u[i] = (T)((double)b[i] / tv.omega);
+  for (int n = 1 + threadIdx.x; n <= NT; n += blockDim.x)
+    u[(size_t)n * P] = (T)((double)b[(size_t)n * P] / tv.omega);
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  // FP64 rows: prev (previous step, node 0 = 0 since its column is eliminated) and cur.
+  double* prev = sm;
+  double* cur = sm + (N + 2);
+  for (int i = 0; i <= N + 1; ++i) prev[i] = 0.0;
+  cur[0] = 0.0;
+  cur[N + 1] = 0.0;
+  for (int step = 1; step <= NT; ++step) {
+    const int n = adj ? NT + 1 - step : step;
+    const bool has_prev = adj ? (n < NT) : (n > 1);
+    const T* bn = b + (size_t)n * P;
+    // forward elimination (cur holds the modified right-hand side)
+    double dp = 0.0;
+    for (int i = 1; i <= N; ++i) {
+      double f = (double)bn[i] * tv.dw[i];
+      if (has_prev) f -= tv.pl[i] * prev[i - 1] + tv.pc[i] * prev[i] + tv.pr[i] * prev[i + 1];
+      dp = (f - tv.lo[i] * dp) * tv.inv[i];
+      cur[i] = dp;
+    }
+    // back substitution
+    for (int i = N - 1; i >= 1; --i) cur[i] = cur[i] - tv.cp[i] * cur[i + 1];
+    T* un = u + (size_t)n * P;
+    for (int i = 1; i <= N; ++i) {
+      un[i] = (T)cur[i];
+      prev[i] = cur[i];
+    }
+  }
+}
+
+// ||r||^2 of r = b - J u from the stored b' (u null: r = b), optionally storing the
+// scaled residual y = (omega/D) r as R.
+template <typename T, typename R, bool ADJ>
+__global__ void __launch_bounds__(kThreads) k_resnorm(LevelView<T> lv, uint32_t total, const T* __restrict__ u,
+                                                      const T* __restrict__ bs, R* __restrict__ y_out,
+                                                      double* __restrict__ partials) {
+  double acc = 0.0;
+  for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+    int n, i;
+    split_index(idx, lv.fd, n, i);
+    const size_t p = (size_t)n * lv.pitch + i;
+    const T y = u ? scaled_residual<T, ADJ>(lv, u, bs, n, i, p) : bs[p];
+    if (y_out) y_out[p] = (R)y;
+    const double r = (double)(unscale(lv, n, i) * y);
+    acc = fma(r, r, acc);
   }
   const double s = block_sum<kThreads>(acc);
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
@@ -216,16 +289,20 @@ __global__ void __launch_bounds__(kThreads) k_add_correction(size_t n, double* _
 }
 
 // Stencil coefficients per node from element k, c (Sec. 2.2 element matrices, Appendix A).
-// m_e = c_e dx / (6 dt) and s_e = k_e / dx; node i touches elements i-1 and i.
+// m_e = c_e dx / (6 dt) and s_e = k_e / dx; node i touches elements i-1 and i.  Also the
+// smoother's scaled coefficients (see stmg_internal.h).
 __global__ void k_build_coef(int N, int pitch, double dx, double dt, double W, double omega,
                              const double* __restrict__ k, const double* __restrict__ c, double* __restrict__ cf64,
                              float* __restrict__ cf32) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= pitch) return;
-  double v[kNumCoef] = {0, 0, 0, 0, 0, 0, 0, 0};
+  double v[kNumCoef];
+#pragma unroll
+  for (int s = 0; s < kNumCoef; ++s) v[s] = 0.0;
   if (i == 0) {
     v[kD] = W;
-    v[kInvD] = omega / W;
+    v[kW] = omega / W;
+    v[kDW] = W / omega;
   } else if (i <= N) {
     const double ml = c[i - 1] * dx / (6.0 * dt), sl = k[i - 1] / dx;
     const double mr = i < N ? c[i] * dx / (6.0 * dt) : 0.0, sr = i < N ? k[i] / dx : 0.0;
@@ -235,7 +312,13 @@ __global__ void k_build_coef(int N, int pitch, double dx, double dt, double W, d
     v[kPL] = i >= 2 ? -ml : 0.0;
     v[kPC] = -2.0 * (ml + mr);
     v[kPR] = i < N ? -mr : 0.0;
-    v[kInvD] = omega / v[kD];
+    v[kW] = omega / v[kD];
+    v[kDW] = v[kD] / omega;
+    v[kSL] = -v[kW] * v[kL];
+    v[kSU] = -v[kW] * v[kU];
+    v[kSPL] = -v[kW] * v[kPL];
+    v[kSPC] = -v[kW] * v[kPC];
+    v[kSPR] = -v[kW] * v[kPR];
   }
 #pragma unroll
   for (int s = 0; s < kNumCoef; ++s) {
@@ -254,18 +337,20 @@ __global__ void k_simp(int N, const double* __restrict__ chi, Simp6 sp, double* 
   c[e] = sp.v[2] + (sp.v[3] - sp.v[2]) * pow(x, sp.v[5]);
 }
 
-// b = B b_Neu with b_Neu,i = dx/2 (q_{i-1} + q_i) for element-wise constant q.
-__global__ void __launch_bounds__(kThreads) k_assemble_load(int N, int NT, int pitch, double dx,
+// b = B b_Neu with b_Neu,i = dx/2 (q_{i-1} + q_i) for element-wise constant q, stored
+// scaled as b' = (omega/D) b.  Writes every value of the padded rows.
+__global__ void __launch_bounds__(kThreads) k_assemble_load(LevelView<double> lv, double dx,
                                                             const double* __restrict__ q, double* __restrict__ b) {
   const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  const long long total = (long long)(NT + 1) * pitch;
+  const long long total = (long long)(lv.NT + 1) * lv.pitch;
   if (idx >= total) return;
-  const int n = (int)(idx / pitch);
-  const int i = (int)(idx - (long long)n * pitch);
+  const int N = lv.N;
+  const int n = (int)(idx / lv.pitch);
+  const int i = (int)(idx - (long long)n * lv.pitch);
   double v = 0.0;
   if (n >= 1 && i >= 1 && i <= N) {
     const double* qn = q + (size_t)n * N;
-    v = 0.5 * dx * (qn[i - 1] + (i < N ? qn[i] : 0.0));
+    v = lv.coef[kW * lv.pitch + i] * (0.5 * dx * (qn[i - 1] + (i < N ? qn[i] : 0.0)));
   }
   b[idx] = v;
 }
@@ -321,37 +406,53 @@ __global__ void k_sens_final(int N, int chunks, const double* __restrict__ chi, 
 // ------------------------------------------------------------------------------ launchers
 
 template <typename T>
-cudaError_t launch_jacobi(const LevelView<T>& lv, bool adj, const T* u, const T* b, T* uo, cudaStream_t s) {
-  const unsigned g = blocks_for((long long)(lv.NT + 1) * (lv.N + 1));
-  if (adj) k_jacobi<T, true><<<g, kThreads, 0, s>>>(lv, u, b, uo);
-  else k_jacobi<T, false><<<g, kThreads, 0, s>>>(lv, u, b, uo);
+inline uint32_t dofs(const LevelView<T>& lv) {
+  return (uint32_t)((uint64_t)(lv.NT + 1) * (uint64_t)(lv.N + 1));
+}
+
+template <typename T>
+cudaError_t launch_sweep(const LevelView<T>& lv, bool adj, const T* u, const T* bs, T* uo, cudaStream_t s) {
+  const uint32_t n = dofs(lv);
+  if (adj) k_sweep<T, true><<<blocks_for(n), kThreads, 0, s>>>(lv, n, u, bs, uo);
+  else k_sweep<T, false><<<blocks_for(n), kThreads, 0, s>>>(lv, n, u, bs, uo);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_sweep_norm(const LevelView<T>& lv, bool adj, const T* u, const T* bs, T* uo, double* partials,
+                              double* out, cudaStream_t s) {
+  const uint32_t n = dofs(lv);
+  if (adj) k_sweep_norm<T, true><<<kNormBlocks, kThreads, 0, s>>>(lv, n, u, bs, uo, partials);
+  else k_sweep_norm<T, false><<<kNormBlocks, kThreads, 0, s>>>(lv, n, u, bs, uo, partials);
+  k_final_sum<<<1, 1024, 0, s>>>(partials, kNormBlocks, out);
   count_launches(2);
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_residual(const LevelView<T>& lv, bool adj, const T* u, const T* b, T* r, cudaStream_t s) {
-  const unsigned g = blocks_for((long long)(lv.NT + 1) * (lv.N + 1));
-  if (adj) k_residual<T, true, 0><<<g, kThreads, 0, s>>>(lv, u, b, r);
-  else k_residual<T, false, 0><<<g, kThreads, 0, s>>>(lv, u, b, r);
-  count_launches(2);
+cudaError_t launch_residual(const LevelView<T>& lv, bool adj, const T* u, const T* bs, T* r, cudaStream_t s) {
+  const uint32_t n = dofs(lv);
+  if (adj) k_residual<T, true, 0><<<blocks_for(n), kThreads, 0, s>>>(lv, n, u, bs, r);
+  else k_residual<T, false, 0><<<blocks_for(n), kThreads, 0, s>>>(lv, n, u, bs, r);
+  count_launches(1);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_apply(const LevelView<T>& lv, bool adj, const T* u, T* y, cudaStream_t s) {
-  const unsigned g = blocks_for((long long)(lv.NT + 1) * (lv.N + 1));
-  if (adj) k_residual<T, true, 1><<<g, kThreads, 0, s>>>(lv, u, nullptr, y);
-  else k_residual<T, false, 1><<<g, kThreads, 0, s>>>(lv, u, nullptr, y);
-  count_launches(2);
+  const uint32_t n = dofs(lv);
+  if (adj) k_residual<T, true, 1><<<blocks_for(n), kThreads, 0, s>>>(lv, n, u, nullptr, y);
+  else k_residual<T, false, 1><<<blocks_for(n), kThreads, 0, s>>>(lv, n, u, nullptr, y);
+  count_launches(1);
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_restrict(int type, int Nf, int NTf, int pf, const T* r, int Nc, int NTc, int pc, T* bc,
+cudaError_t launch_restrict(int type, int Nf, int NTf, int pf, const T* r, const LevelView<T>& cv, T* bc,
                             cudaStream_t s) {
-  k_restrict<T><<<blocks_for((long long)(NTc + 1) * (Nc + 1)), kThreads, 0, s>>>(type, Nf, NTf, pf, r, Nc, NTc,
-                                                                                   pc, bc);
+  const uint32_t n = dofs(cv);
+  k_restrict<T><<<blocks_for(n), kThreads, 0, s>>>(type, Nf, NTf, pf, r, cv, n, bc);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -359,8 +460,10 @@ cudaError_t launch_restrict(int type, int Nf, int NTf, int pf, const T* r, int N
 template <typename T>
 cudaError_t launch_prolong_add(int type, int Nf, int NTf, int pf, T* u, int Nc, int NTc, int pc, const T* z,
                                cudaStream_t s) {
-  k_prolong_add<T><<<blocks_for((long long)(NTf + 1) * (Nf + 1)), kThreads, 0, s>>>(type, Nf, NTf, pf, u, Nc, NTc,
-                                                                                      pc, z);
+  (void)Nc;
+  (void)NTc;
+  const uint32_t n = (uint32_t)((uint64_t)(NTf + 1) * (uint64_t)(Nf + 1));
+  k_prolong_add<T><<<blocks_for(n), kThreads, 0, s>>>(type, make_fastdiv(Nf + 1), n, pf, u, pc, z);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -377,19 +480,33 @@ cudaError_t launch_exact(const ThomasView& tv, bool adj, const T* b, T* u, cudaS
   return cudaGetLastError();
 }
 
-template <typename T, typename R>
-cudaError_t launch_resnorm(const LevelView<T>& lv, bool adj, const T* u, const T* b, R* r_out, double* partials,
-                           double* out, cudaStream_t s) {
-  if (adj) k_resnorm<T, R, true><<<kNormBlocks, kThreads, 0, s>>>(lv, u, b, r_out, partials);
-  else k_resnorm<T, R, false><<<kNormBlocks, kThreads, 0, s>>>(lv, u, b, r_out, partials);
-  k_final_sum<<<1, 1024, 0, s>>>(partials, kNormBlocks, out);
-  count_launches(3);
+template <typename T>
+cudaError_t launch_scale(const LevelView<T>& lv, bool to_scaled, T* x, cudaStream_t s) {
+  const uint32_t n = dofs(lv);
+  k_scale<T><<<blocks_for(n), kThreads, 0, s>>>(lv, n, to_scaled, x);
+  count_launches(1);
   return cudaGetLastError();
 }
 
-cudaError_t launch_defect(const LevelView<double>& lv, bool adj, const double* u, const double* b, float* r32,
+template <typename T>
+cudaError_t launch_resnorm(const LevelView<T>& lv, bool adj, const T* u, const T* bs, double* partials, double* out,
+                           cudaStream_t s) {
+  const uint32_t n = dofs(lv);
+  if (adj) k_resnorm<T, T, true><<<kNormBlocks, kThreads, 0, s>>>(lv, n, u, bs, (T*)nullptr, partials);
+  else k_resnorm<T, T, false><<<kNormBlocks, kThreads, 0, s>>>(lv, n, u, bs, (T*)nullptr, partials);
+  k_final_sum<<<1, 1024, 0, s>>>(partials, kNormBlocks, out);
+  count_launches(2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_defect(const LevelView<double>& lv, bool adj, const double* u, const double* bs, float* ys32,
                           double* partials, double* out, cudaStream_t s) {
-  return launch_resnorm<double, float>(lv, adj, u, b, r32, partials, out, s);
+  const uint32_t n = dofs(lv);
+  if (adj) k_resnorm<double, float, true><<<kNormBlocks, kThreads, 0, s>>>(lv, n, u, bs, ys32, partials);
+  else k_resnorm<double, float, false><<<kNormBlocks, kThreads, 0, s>>>(lv, n, u, bs, ys32, partials);
+  k_final_sum<<<1, 1024, 0, s>>>(partials, kNormBlocks, out);
+  count_launches(2);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_add_correction(size_t n, double* u, const float* e, cudaStream_t s) {
@@ -418,8 +535,9 @@ cudaError_t launch_simp(int N, const double* chi, Simp6 sp, double* k, double* c
   return cudaGetLastError();
 }
 
-cudaError_t launch_assemble_load(int N, int NT, int pitch, double dx, const double* q, double* b, cudaStream_t s) {
-  k_assemble_load<<<blocks_for((long long)(NT + 1) * pitch), kThreads, 0, s>>>(N, NT, pitch, dx, q, b);
+cudaError_t launch_assemble_load(const LevelView<double>& lv, double dx, const double* q, double* bs,
+                                 cudaStream_t s) {
+  k_assemble_load<<<blocks_for((long long)(lv.NT + 1) * lv.pitch), kThreads, 0, s>>>(lv, dx, q, bs);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -434,15 +552,25 @@ cudaError_t launch_sensitivity(int N, int NT, int pitch, double dx, double dt, c
   return cudaGetLastError();
 }
 
-#define STMG_INST(T)                                                                                            \
-  template cudaError_t launch_jacobi<T>(const LevelView<T>&, bool, const T*, const T*, T*, cudaStream_t);       \
-  template cudaError_t launch_residual<T>(const LevelView<T>&, bool, const T*, const T*, T*, cudaStream_t);     \
-  template cudaError_t launch_apply<T>(const LevelView<T>&, bool, const T*, T*, cudaStream_t);                  \
-  template cudaError_t launch_restrict<T>(int, int, int, int, const T*, int, int, int, T*, cudaStream_t);       \
-  template cudaError_t launch_prolong_add<T>(int, int, int, int, T*, int, int, int, const T*, cudaStream_t);    \
-  template cudaError_t launch_exact<T>(const ThomasView&, bool, const T*, T*, cudaStream_t);                    \
-  template cudaError_t launch_resnorm<T, T>(const LevelView<T>&, bool, const T*, const T*, T*, double*, double*, \
-                                            cudaStream_t);
+cudaError_t launch_sens_final(int N, int chunks, const double* chi, Simp6 sp, const double* scratch, double* g,
+                              cudaStream_t s) {
+  k_sens_final<<<blocks_for(N), kThreads, 0, s>>>(N, chunks, chi, sp, scratch, g);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+#define STMG_INST(T)                                                                                              \
+  template cudaError_t launch_sweep<T>(const LevelView<T>&, bool, const T*, const T*, T*, cudaStream_t);          \
+  template cudaError_t launch_sweep_norm<T>(const LevelView<T>&, bool, const T*, const T*, T*, double*, double*,  \
+                                            cudaStream_t);                                                        \
+  template cudaError_t launch_residual<T>(const LevelView<T>&, bool, const T*, const T*, T*, cudaStream_t);       \
+  template cudaError_t launch_apply<T>(const LevelView<T>&, bool, const T*, T*, cudaStream_t);                    \
+  template cudaError_t launch_restrict<T>(int, int, int, int, const T*, const LevelView<T>&, T*, cudaStream_t);   \
+  template cudaError_t launch_prolong_add<T>(int, int, int, int, T*, int, int, int, const T*, cudaStream_t);      \
+  template cudaError_t launch_exact<T>(const ThomasView&, bool, const T*, T*, cudaStream_t);                      \
+  template cudaError_t launch_scale<T>(const LevelView<T>&, bool, T*, cudaStream_t);                              \
+  template cudaError_t launch_resnorm<T>(const LevelView<T>&, bool, const T*, const T*, double*, double*,         \
+                                         cudaStream_t);
 STMG_INST(double)
 STMG_INST(float)
 #undef STMG_INST

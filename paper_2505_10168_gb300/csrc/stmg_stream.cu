@@ -1,0 +1,271 @@
+// stmg_stream.cu -- fused FP32 passes of the V-cycle for the mixed-precision scheme.
+//
+// One warp owns a window of 128 columns (4 per lane, float4) of one level and marches
+// through a chunk of time rows.  Because the space-time stencil couples row n only to
+// rows n and n-1 (n+1 for the adjoint), S damped-Jacobi sweeps (Sec. 3.1) are a pipeline
+// over rows: sweep k of row n needs sweep k-1 of rows n and n-1, so a warp keeps the
+// previous row of every stage in registers and produces all S sweeps of a row as soon as
+// the row is read.  The same pipeline then evaluates the residual and restricts it
+// (Sec. 3.1, R = s P^T) to the coarse level (DOWN pass), or adds the prolongated coarse
+// correction before sweeping (UP pass).  x-neighbours come from warp shuffles; the window
+// carries an 8-column halo on each side and a chunk starts S(+1) rows early, so every
+// output value is computed from exact inputs with no block-level synchronisation.
+//
+// HBM traffic per DOF of a level (x-coarsening, zero start): DOWN reads b' and writes u
+// and b'_c (10 B); UP reads u, b', z and writes u (14 B); the finest-level UP of the
+// mixed scheme adds its result straight into the FP64 iterate instead (26 B).
+#include "stmg_internal.h"
+#include "stmg_stream.h"
+
+namespace stmg {
+namespace {
+
+constexpr int kVec = 4;
+constexpr int kWin = 32 * kVec;            // columns per warp window
+constexpr int kHalo = 8;                   // halo columns on each side
+constexpr int kOwn = kWin - 2 * kHalo;     // 112 columns owned per window
+constexpr int kWarpsPerBlock = 4;
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ float4 f4zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+
+__device__ __forceinline__ float4 ld4(const float* __restrict__ p, size_t off, bool ok) {
+  return ok ? __ldg(reinterpret_cast<const float4*>(p + off)) : f4zero();
+}
+
+// One stage of the pipeline on a lane's 4 columns: out = a*x + b' + sum_k S_k x_k, with
+// a = 1 - omega for a sweep and a = -omega for the scaled residual.
+__device__ __forceinline__ float4 stage(float a, const float4& x, const float4& px, const float4& b, bool dir_row,
+                                        bool has_prev, const float4& sl, const float4& su, const float4& spl,
+                                        const float4& spc, const float4& spr, int lane) {
+  float xl = __shfl_up_sync(kFull, x.w, 1);
+  float xr = __shfl_down_sync(kFull, x.x, 1);
+  float pl = __shfl_up_sync(kFull, px.w, 1);
+  float pr = __shfl_down_sync(kFull, px.x, 1);
+  if (lane == 0) xl = pl = 0.f;
+  if (lane == 31) xr = pr = 0.f;
+  float4 o;
+  o.x = fmaf(a, x.x, b.x);
+  o.y = fmaf(a, x.y, b.y);
+  o.z = fmaf(a, x.z, b.z);
+  o.w = fmaf(a, x.w, b.w);
+  if (!dir_row) {
+    o.x = fmaf(sl.x, xl, o.x);
+    o.x = fmaf(su.x, x.y, o.x);
+    o.y = fmaf(sl.y, x.x, o.y);
+    o.y = fmaf(su.y, x.z, o.y);
+    o.z = fmaf(sl.z, x.y, o.z);
+    o.z = fmaf(su.z, x.w, o.z);
+    o.w = fmaf(sl.w, x.z, o.w);
+    o.w = fmaf(su.w, xr, o.w);
+    if (has_prev) {
+      o.x = fmaf(spl.x, pl, o.x);
+      o.x = fmaf(spc.x, px.x, o.x);
+      o.x = fmaf(spr.x, px.y, o.x);
+      o.y = fmaf(spl.y, px.x, o.y);
+      o.y = fmaf(spc.y, px.y, o.y);
+      o.y = fmaf(spr.y, px.z, o.y);
+      o.z = fmaf(spl.z, px.y, o.z);
+      o.z = fmaf(spc.z, px.z, o.z);
+      o.z = fmaf(spr.z, px.w, o.z);
+      o.w = fmaf(spl.w, px.z, o.w);
+      o.w = fmaf(spc.w, px.w, o.w);
+      o.w = fmaf(spr.w, pr, o.w);
+    }
+  }
+  return o;
+}
+
+// MODE: 0 plain sweeps, 1 sweeps + residual + x-restriction, 2 sweeps + residual +
+// t-restriction, 3 x-prolongation + sweeps, 4 t-prolongation + sweeps.
+template <bool ADJ, int S, int MODE>
+__global__ void __launch_bounds__(32 * kWarpsPerBlock) k_stream(StreamArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int wid = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  if (wid >= a.strips * a.chunks) return;  // the whole warp leaves together
+  const int strip = wid % a.strips;
+  const int chunk = wid / a.strips;
+  const int c0 = strip * kOwn - kHalo;
+  const int col = c0 + kVec * lane;  // multiple of 4; either fully inside [0, pitch) or fully outside
+  const bool inside = col >= 0 && col + kVec <= a.pitch;
+  const bool owner = lane >= kHalo / kVec && lane < (kHalo + kOwn) / kVec && inside;
+  const int P = a.pitch;
+
+  const float4 sl = ld4(a.coef, (size_t)kSL * P + col, inside);
+  const float4 su = ld4(a.coef, (size_t)kSU * P + col, inside);
+  const float4 spl = ld4(a.coef, (size_t)kSPL * P + col, inside);
+  const float4 spc = ld4(a.coef, (size_t)kSPC * P + col, inside);
+  const float4 spr = ld4(a.coef, (size_t)kSPR * P + col, inside);
+  constexpr bool DOWN = MODE == 1 || MODE == 2;
+  float4 dw = f4zero();
+  if (DOWN) dw = ld4(a.coef, (size_t)kDW * P + col, inside);
+  // coarse scaling of the restricted residual: x: coarse nodes col/2 and col/2 + 1;
+  // t: coarse node = fine node
+  float2 cwx = make_float2(0.f, 0.f);
+  float4 cwt = f4zero();
+  if (MODE == 1 && inside && col / 2 + 1 < a.pc) {
+    cwx.x = a.ccoef[(size_t)kW * a.pc + col / 2];
+    cwx.y = a.ccoef[(size_t)kW * a.pc + col / 2 + 1];
+  }
+  if (MODE == 2) cwt = ld4(a.ccoef, (size_t)kW * a.pc + col, inside);
+
+  const int n0 = chunk * a.rows;
+  const int n1 = min(a.NT + 1, n0 + a.rows);
+  constexpr int WARM = DOWN ? S + 1 : S;
+  const int first = ADJ ? min(a.NT, n1 - 1 + WARM) : max(0, n0 - WARM);
+  const int last = ADJ ? n0 : n1 - 1;
+  const int step = ADJ ? -1 : 1;
+
+  float4 prev[S + 1];
+#pragma unroll
+  for (int k = 0; k <= S; ++k) prev[k] = f4zero();
+  float4 held = f4zero();  // t-restriction: residual of the first row of a pair
+
+  for (int n = first;; n += step) {
+    const bool emit = n >= n0 && n < n1;
+    const bool dir_row = n == 0;
+    const bool has_prev = ADJ ? (n < a.NT) : (n > 1);
+    const size_t rowoff = (size_t)n * P;
+    const float4 b = ld4(a.bs, rowoff + col, inside);
+    float4 cur[S + 1];
+    if (a.zero_init) cur[0] = f4zero();
+    else cur[0] = ld4(a.u_in, rowoff + col, inside);
+    if (MODE == 3) {
+      // x-prolongation: fine 2j <- z_j, fine 2j+1 <- (z_j + z_{j+1}) / 2
+      const int ca = col / 2;  // even
+      const bool zin = col >= 0 && ca + 1 < a.pc;
+      float2 zz = make_float2(0.f, 0.f);
+      if (zin) zz = __ldg(reinterpret_cast<const float2*>(a.z + (size_t)n * a.pc + ca));
+      float z2 = __shfl_down_sync(kFull, zz.x, 1);
+      if (lane == 31) z2 = (col >= 0 && ca + 2 < a.pc) ? a.z[(size_t)n * a.pc + ca + 2] : 0.f;
+      if (col + 0 >= 0 && col + 0 <= a.N) cur[0].x += zz.x;
+      if (col + 1 >= 0 && col + 1 <= a.N) cur[0].y += 0.5f * (zz.x + zz.y);
+      if (col + 2 >= 0 && col + 2 <= a.N) cur[0].z += zz.y;
+      if (col + 3 >= 0 && col + 3 <= a.N) cur[0].w += 0.5f * (zz.y + z2);
+    } else if (MODE == 4) {
+      // causal t-prolongation: fine rows 2m and 2m+1 <- coarse row m
+      const float4 zz = ld4(a.z, (size_t)(n >> 1) * a.pc + col, inside);
+      if (col + 0 <= a.N) cur[0].x += zz.x;
+      if (col + 1 <= a.N) cur[0].y += zz.y;
+      if (col + 2 <= a.N) cur[0].z += zz.z;
+      if (col + 3 <= a.N) cur[0].w += zz.w;
+    }
+#pragma unroll
+    for (int k = 1; k <= S; ++k) {
+      if (k == 1 && a.zero_init) cur[1] = b;  // a sweep from zero is exactly b'
+      else cur[k] = stage(a.omc, cur[k - 1], prev[k - 1], b, dir_row, has_prev, sl, su, spl, spc, spr, lane);
+    }
+    if (emit && owner) {
+      if (a.u64) {
+        double2* q = reinterpret_cast<double2*>(a.u64 + rowoff + col);
+        double2 lo = q[0], hi = q[1];
+        lo.x += (double)cur[S].x;
+        lo.y += (double)cur[S].y;
+        hi.x += (double)cur[S].z;
+        hi.y += (double)cur[S].w;
+        q[0] = lo;
+        q[1] = hi;
+      } else {
+        *reinterpret_cast<float4*>(a.u_out + rowoff + col) = cur[S];
+      }
+    }
+    if (DOWN) {
+      // scaled residual y = b' - omega u + sum S_k u_k, r = (D / omega) y
+      const float4 y = stage(-a.omega, cur[S], prev[S], b, dir_row, has_prev, sl, su, spl, spc, spr, lane);
+      float4 r;
+      if (dir_row) {
+        r = make_float4(a.Wo * y.x, a.Wo * y.y, a.Wo * y.z, a.Wo * y.w);
+      } else {
+        r = make_float4(dw.x * y.x, dw.y * y.y, dw.z * y.z, dw.w * y.w);
+      }
+      if (MODE == 1) {
+        float rl = __shfl_up_sync(kFull, r.w, 1);
+        if (lane == 0) rl = 0.f;
+        if (emit && owner) {
+          // b_c[j] = r[2j] + (r[2j-1] + r[2j+1]) / 2, scaled by omega / D_c
+          const int j0 = col / 2;
+          const float s0 = (n == 0 || j0 == 0) ? a.cwW : cwx.x;
+          const float s1 = (n == 0) ? a.cwW : cwx.y;
+          float* out = a.bc + (size_t)n * a.pc;
+          if (col <= a.N) out[j0] = s0 * (r.x + 0.5f * (rl + r.y));
+          if (col + 2 <= a.N) out[j0 + 1] = s1 * (r.z + 0.5f * (r.y + r.w));
+        }
+      } else {
+        // b_c[m] = (r[2m] + r[2m+1]) / 2 (causal P^T with s = 1/2), scaled by omega / D_c
+        const bool second = ADJ ? (n % 2 == 0) : (n % 2 == 1 || n == a.NT);
+        if (second) {
+          float4 sum = r;
+          if (ADJ ? (n + 1 <= a.NT) : (n % 2 == 1)) {
+            sum.x += held.x;
+            sum.y += held.y;
+            sum.z += held.z;
+            sum.w += held.w;
+          }
+          if (emit && owner) {
+            const int m = n >> 1;
+            float4 sc = cwt;
+            if (m == 0) sc = make_float4(a.cwW, a.cwW, a.cwW, a.cwW);
+            float4 o = make_float4(0.5f * sc.x * sum.x, 0.5f * sc.y * sum.y, 0.5f * sc.z * sum.z,
+                                   0.5f * sc.w * sum.w);
+            *reinterpret_cast<float4*>(a.bc + (size_t)m * a.pc + col) = o;
+          }
+          held = f4zero();
+        } else {
+          held = r;
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k <= S; ++k) prev[k] = cur[k];
+    if (n == last) break;
+  }
+}
+
+template <bool ADJ, int MODE>
+cudaError_t launch_mode(const StreamArgs& a, int S, unsigned grid, cudaStream_t s) {
+  switch (S) {
+    case 1: k_stream<ADJ, 1, MODE><<<grid, 32 * kWarpsPerBlock, 0, s>>>(a); break;
+    case 2: k_stream<ADJ, 2, MODE><<<grid, 32 * kWarpsPerBlock, 0, s>>>(a); break;
+    case 3: k_stream<ADJ, 3, MODE><<<grid, 32 * kWarpsPerBlock, 0, s>>>(a); break;
+    case 4: k_stream<ADJ, 4, MODE><<<grid, 32 * kWarpsPerBlock, 0, s>>>(a); break;
+    case 5: k_stream<ADJ, 5, MODE><<<grid, 32 * kWarpsPerBlock, 0, s>>>(a); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+void stream_layout(int N, int NT, StreamArgs& a) {
+  a.strips = (N + 1 + kOwn - 1) / kOwn;
+  // about 24 warps per SM on 152 SMs, chunks of an even number of rows in [16, 256]
+  const long long target = 152LL * 24;
+  long long rows = ((long long)(NT + 1) * a.strips + target - 1) / target;
+  rows = rows < 16 ? 16 : (rows > 256 ? 256 : rows);
+  rows += rows & 1;
+  a.rows = (int)rows;
+  a.chunks = (NT + 1 + a.rows - 1) / a.rows;
+}
+
+cudaError_t launch_stream(int mode, bool adj, int S, const StreamArgs& a, cudaStream_t s) {
+  const long long warps = (long long)a.strips * a.chunks;
+  const unsigned grid = (unsigned)((warps + kWarpsPerBlock - 1) / kWarpsPerBlock);
+  cudaError_t e = cudaErrorInvalidValue;
+  switch (mode * 2 + (adj ? 1 : 0)) {
+    case 0: e = launch_mode<false, 0>(a, S, grid, s); break;
+    case 1: e = launch_mode<true, 0>(a, S, grid, s); break;
+    case 2: e = launch_mode<false, 1>(a, S, grid, s); break;
+    case 3: e = launch_mode<true, 1>(a, S, grid, s); break;
+    case 4: e = launch_mode<false, 2>(a, S, grid, s); break;
+    case 5: e = launch_mode<true, 2>(a, S, grid, s); break;
+    case 6: e = launch_mode<false, 3>(a, S, grid, s); break;
+    case 7: e = launch_mode<true, 3>(a, S, grid, s); break;
+    case 8: e = launch_mode<false, 4>(a, S, grid, s); break;
+    case 9: e = launch_mode<true, 4>(a, S, grid, s); break;
+    default: break;
+  }
+  count_launches(1);
+  return e;
+}
+
+}  // namespace stmg

@@ -1,0 +1,34 @@
+// stmg_stream.h -- fused FP32 V-cycle passes (stmg_stream.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+namespace stmg {
+
+enum StreamMode { kStreamPlain = 0, kStreamDownX = 1, kStreamDownT = 2, kStreamUpX = 3, kStreamUpT = 4 };
+
+struct StreamArgs {
+  // this level (FP32 arrays in the padded layout of stmg_internal.h)
+  int N, NT, pitch;
+  float omega, omc, Wo;    // omega, 1 - omega, W_Diri / omega
+  const float* coef;       // kNumCoef * pitch
+  const float* u_in;       // starting iterate (ignored when zero_init)
+  const float* bs;         // scaled right-hand side b'
+  float* u_out;            // result, or nullptr when u64 is set
+  double* u64;             // finest level of the mixed scheme: u64 += result
+  int zero_init;           // the starting iterate is 0
+  // coarse level: restriction target (DOWN) or correction source (UP)
+  int pc;                  // coarse pitch
+  const float* ccoef;      // coarse coefficients (DOWN)
+  float cwW;               // coarse omega / W_Diri (DOWN)
+  float* bc;               // coarse scaled right-hand side (DOWN)
+  const float* z;          // coarse correction (UP)
+  // work decomposition (stream_layout)
+  int rows, strips, chunks;
+};
+
+// Fills rows / strips / chunks for a level of N elements and NT steps.
+void stream_layout(int N, int NT, StreamArgs& a);
+// S sweeps (1..5) in one pass of the given mode; adj selects J^T.
+cudaError_t launch_stream(int mode, bool adj, int S, const StreamArgs& a, cudaStream_t s);
+
+}  // namespace stmg

@@ -140,6 +140,24 @@ def test_vcycle_iterates_match_oracle(i, adj):
     g.close()
 
 
+@pytest.mark.parametrize("i", range(len(CASES)))
+@pytest.mark.parametrize("adj", [False, True])
+@pytest.mark.parametrize("nu", [5, 7])
+def test_fp32_cycle_matches_oracle_cycle(i, adj, nu):
+    """One mixed-precision step from u = 0 is exactly one FP32 V-cycle on J e = b, so it
+    must equal the oracle's FP64 V-cycle from zero up to FP32 rounding (amplified by the
+    coarse solves); this checks the fused FP32 passes directly, which the outer FP64
+    correction would otherwise hide."""
+    N, NT, L, tT, k, c = _case(i)
+    g, o = _pair(N, NT, L, tT, k, c, max_coarse_dofs=64, nu=nu, precision="mixed")
+    b = _rand_vec(3, o.shape(0))
+    ug = np.zeros(o.shape(0))
+    g.vcycle(ug, b, adjoint=adj)
+    uo = o.vcycle(np.zeros(o.shape(0)), b, adj=adj)
+    assert rel(ug, uo) < 2e-4
+    g.close()
+
+
 @pytest.mark.parametrize("reasm", ["R", "K"])
 def test_config1_solve_matches_oracle(reasm):
     w = wl.config1()
