@@ -45,6 +45,9 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-variant", action="store_true", help="skip the other-precision solve of the same workload")
+    p.add_argument("--serving-requests", type=int, default=64,
+                   help="requests of the 512-request serving trace to replay (0: skip serving)")
+    p.add_argument("--serving-workers", type=int, default=6)
     return p.parse_args()
 
 
@@ -196,10 +199,53 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "%s_timeslab%d" % (w["name"], nt_sample), "N": w["N"], "NT": nt_sample},
+        "config": {"workload": w["name"], "N": w["N"], "NT": w["NT"], "dofs": (w["N"] + 1) * (w["NT"] + 1),
+                   "precision": "fp64", "tol": TOL, "sample": "first %d time steps per step" % nt_sample},
         "cpu_baseline": {"value": value, "unit": "DOF/s", "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "DOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
+
+
+# ----------------------------------------------------------------------------- ranks
+def max_over_ranks(x, world, device="cpu"):
+    """The slowest rank's value (every rank gets it); identity on one rank."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, seconds):
+    """Aggregate throughput of independent replicas: every rank's units / the slowest rank's time."""
+    return world * units_per_rank / seconds
+
+
+# ----------------------------------------------------------------------------- serving
+SERVING_OPTS = dict(precision="mixed", tol=TOL, nu=20, max_cycles=300)
+
+
+def run_serving(nreq, workers):
+    """Closed loop (all requests queued at once) for throughput, then the same requests
+    with their Poisson gaps rescaled to 0.8x that throughput for latency."""
+    from paper_2505_10168_gb300 import serving as sv
+    from paper_2505_10168_gb300 import workloads as wl
+
+    reqs = wl.serving_requests()[:nreq]
+    fields = lambda r: wl.request_fields(r)[:2]  # noqa: E731
+    with sv.Server(workers=workers) as srv:
+        sv.replay(srv, reqs[: min(4, nreq)], fields, speed=1e9, **SERVING_OPTS)  # warm-up
+        _, closed = sv.replay(srv, reqs, fields, speed=1e9, **SERVING_OPTS)
+        rate = closed["requests"] / closed["makespan_s"]  # requests per second
+        mean_gap = (reqs[-1]["arrival"] - reqs[0]["arrival"]) / max(1, len(reqs) - 1)
+        speed = 0.8 * rate * mean_gap
+        _, poisson = sv.replay(srv, reqs, fields, speed=speed, **SERVING_OPTS)
+    return {"requests": nreq, "of": 512, "workers": workers, "solver": SERVING_OPTS,
+            "closed_loop": closed, "poisson_0.8": poisson,
+            "p50_s": poisson["p50_s"], "p99_s": poisson["p99_s"], "dofs_per_s": closed["dofs_per_s"]}
 
 
 # ----------------------------------------------------------------------------- GPU arm
@@ -242,6 +288,7 @@ def main():
     t0 = time.perf_counter()
     solver = pkg.Solver(N, NT, L, tT, k, c, precision=args.precision, tol=TOL)
     setup_ms = 1e3 * (time.perf_counter() - t0)
+    levels, path = solver.num_levels, solver.path()
 
     for _ in range(args.warmup):
         st, cyc, rr = solver.solve(u, q=q)
@@ -263,13 +310,9 @@ def main():
     launches = pkg.kernel_launches() - l0
     clocks = clk.stop()
     barrier()
-    ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1), world, dev)
     ms_per_step = ms / args.steps
-    value = world * dofs * args.steps / (ms * 1e-3)
+    value = whole_job_rate(dofs * args.steps, world, ms * 1e-3)
     cycles = statuses[-1][1]
     relres = statuses[-1][2]
     ok = all(s[0] == "ok" and s[2] < TOL for s in statuses)
@@ -305,6 +348,28 @@ def main():
     except Exception as ex:  # report, do not hide
         roofline = {"error": repr(ex)}
 
+    # ---- GPU competitor: exact sequential time stepping (one block, all NT steps) ----
+    gpu_ts = None
+    try:
+        b = torch.empty_like(u)
+        solver.assemble_load(q, b)
+        row0 = torch.zeros((1, N + 1), dtype=torch.float64, device=dev)  # T = 0 at t = 0
+        ut = torch.empty_like(u)
+        solver.recompute_slabs(b, row0, NT, ut)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        solver.recompute_slabs(b, row0, NT, ut)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts_ms = e0.elapsed_time(e1)
+        gpu_ts = {"value": dofs / (ts_ms * 1e-3), "unit": "DOF/s", "ms_per_solve": ts_ms,
+                  "what": "exact solution by sequential implicit time stepping on the GPU: one block, one "
+                          "block-scan Thomas solve per time step (not STMG; the sequential-in-time competitor)"}
+        del b, ut
+    except Exception as ex:
+        gpu_ts = {"error": repr(ex)}
+
     # ---- end to end through the C ABI with host buffers ----
     e2e = None
     if not args.no_e2e:
@@ -317,12 +382,8 @@ def main():
         for _ in range(ksteps):
             solver.solve(uh, q=qh)
         torch.cuda.synchronize()
-        el = time.perf_counter() - t1
-        if world > 1:
-            t = torch.tensor([el], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            el = float(t.item())
-        e2e = {"value": world * dofs * ksteps / el, "unit": "DOF/s", "h2d_bytes_per_step": int(qh.numel() * 8),
+        el = max_over_ranks(time.perf_counter() - t1, world, dev)
+        e2e = {"value": whole_job_rate(dofs * ksteps, world, el), "unit": "DOF/s", "h2d_bytes_per_step": int(qh.numel() * 8),
                "d2h_bytes_per_step": int(uh.numel() * 8 + 8 * (cycles + 2)), "steps": ksteps}
         del qh, uh
 
@@ -347,6 +408,14 @@ def main():
                    "dtype": "f64" if other == "fp64" else "f32+f64"}
         s2.close()
 
+    # ---- serving: continuous batching of the uneven forward/adjoint request trace ----
+    serving = None
+    if args.serving_requests > 0:
+        del u, q
+        solver.close()
+        torch.cuda.empty_cache()
+        serving = run_serving(args.serving_requests, args.serving_workers)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_obj(w)
@@ -358,12 +427,12 @@ def main():
             "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
             "data": "synthetic",
             "config": {"workload": w["name"], "N": N, "NT": NT, "dofs": dofs, "precision": args.precision,
-                       "tol": TOL, "levels": solver.num_levels, "path": solver.path(), "cycles": cycles,
+                       "tol": TOL, "levels": levels, "path": path, "cycles": cycles,
                        "relres": relres, "converged": ok, "setup_ms": setup_ms,
                        "l2": "no flush: every vector (%d MB) exceeds the 129 MB L2" % (dofs * 8 // 2 ** 20),
                        "parallelism": "replicas" if world > 1 else "single"},
             "clocks": clocks, "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline,
-            "cpu_baseline": cpu, "variant": variant,
+            "cpu_baseline": cpu, "variant": variant, "gpu_time_stepping": gpu_ts, "serving": serving,
         }
         print(json.dumps(out))
     if world > 1:

@@ -38,6 +38,8 @@
 #ifndef STMG_H
 #define STMG_H
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -76,6 +78,8 @@ typedef struct {
     double tol;                /* [1e-10] stop when ||J u - b|| / ||b|| < tol (Sec. 3.1) */
     double div_tol;            /* [1e9] stop (diverged) when the relative residual exceeds this */
     int max_cycles;            /* [100] cycle limit (Sec. 3.1) */
+    int mixed_first_cycles;    /* [3] STMG_MIXED: FP32 V-cycles run on the first defect (an inner
+                                  iteration) before the first FP64 correction; each counts as a cycle */
 } stmg_opts;
 
 void stmg_default_opts(stmg_opts* opts);
@@ -87,6 +91,32 @@ void stmg_default_opts(stmg_opts* opts);
  * vectors.  opts NULL = defaults.  stream: a cudaStream_t or NULL. */
 stmg_status stmg_create(stmg_t* handle, int nel, int nt, double L, double t_end, const double* k_el,
                         const double* c_el, const stmg_opts* opts, void* stream);
+
+/* Device memory hooks: alloc(bytes, ctx) returns device memory of the current device,
+ * aligned to 256 bytes, or NULL when it has none left (the call then fails with
+ * STMG_ENOMEM); free(ptr, ctx) returns it.  Both are called only from the host thread
+ * that is inside an stmg call on this handle.  stmg_create_with_allocator is stmg_create
+ * with every device allocation of the handle (hierarchy, scratch, staging) taken from
+ * the hooks; give both or neither. */
+typedef void* (*stmg_alloc_fn)(size_t bytes, void* ctx);
+typedef void (*stmg_free_fn)(void* ptr, void* ctx);
+stmg_status stmg_create_with_allocator(stmg_t* handle, int nel, int nt, double L, double t_end,
+                                       const double* k_el, const double* c_el, const stmg_opts* opts, void* stream,
+                                       stmg_alloc_fn alloc, stmg_free_fn free_fn, void* ctx);
+
+/* Issue the handle's future work on another CUDA stream (every call returns with its own
+ * work complete, so nothing is pending on the old one). */
+stmg_status stmg_set_stream(stmg_t handle, void* stream);
+
+/* Bytes of device memory the handle holds now. */
+long long stmg_device_bytes(stmg_t handle);
+
+/* Device bytes that stmg_create would allocate for this problem and these options (the
+ * planner runs on the host; nothing is allocated); k_el, c_el are host arrays.  Solves
+ * with host element loads, checkpointed sensitivities or the per-level building blocks
+ * may add staging buffers.  Returns -1 for invalid arguments. */
+long long stmg_footprint(int nel, int nt, double L, double t_end, const double* k_el, const double* c_el,
+                         const stmg_opts* opts);
 
 /* Replace k and c (same nel); re-runs the planner.  With deff_fixed > 0 the coarsening
  * path, and so every level size, is unchanged (Sec. 7.2); otherwise levels may be
@@ -198,6 +228,61 @@ stmg_status stmg_vcycle(stmg_t handle, int adjoint, double* u, const double* b);
 #define STMG_NOALLOC_MAX_SCRATCH (1 << 20)
 stmg_status stmg_sensitivity_noalloc(int nel, int nt, double L, double t_end, const double* chi, const double* simp6,
                                      const double* u, const double* lam, double* dtheta_dchi, void* stream);
+
+/* ---- serving: continuous batching of forward and adjoint solves ----------------------- */
+/* A server owns worker threads (one CUDA stream each) and one device memory arena of
+ * budget_bytes.  Submitted requests wait in one FIFO queue and start when a worker is free
+ * and their footprint (stmg_footprint, plus staging for an element-load array) fits in the
+ * budget next to the running requests; several requests run at once and their kernels
+ * overlap on the GPU.  Finished hierarchies stay resident in the arena and are reused by
+ * later requests with the same grid and options (cache != 0) until memory is needed.  A
+ * request's result does not depend on what else runs: it is bit-identical alone and in any
+ * mix.  Latencies are measured on the server's steady clock (stmg_server_now). */
+typedef struct stmg_server_s* stmg_server_t;
+
+typedef struct {
+    int workers;            /* [4] concurrent solves */
+    long long budget_bytes; /* [0 = half of the free device memory] arena size */
+    int cache;              /* [1] keep finished hierarchies for reuse */
+} stmg_server_opts;
+
+typedef struct {
+    int nel, nt;
+    double L, t_end;
+    const double* k_el;     /* host, nel values; copied by stmg_server_submit */
+    const double* c_el;     /* host, nel values; copied by stmg_server_submit */
+    const double* q_el;     /* host element loads (nt+1) x nel, kept alive by the caller until the
+                               request completes; or NULL for the uniform load q_value */
+    double q_value;
+    int adjoint;            /* 0: solve J u = b; 1: solve J^T lam = b dt (the compliance adjoint,
+                               Sec. 7.2, with Theta_ref = 1) */
+    double* out;            /* (nt+1) x (nel+1) result (host or device), or NULL */
+    stmg_opts opts;         /* solver options of this request */
+} stmg_request;
+
+typedef struct {
+    int status;             /* stmg_status of the solve, or -1 while queued or running */
+    int cycles;
+    double relres;
+    double theta;           /* b^T x dt of the result x: the compliance, for both directions */
+    double t_submit, t_start, t_end;  /* seconds on the server clock */
+    long long bytes;        /* device bytes the request's hierarchy held */
+    int worker;
+} stmg_result;
+
+void stmg_server_default_opts(stmg_server_opts* opts);
+stmg_status stmg_server_create(stmg_server_t* server, const stmg_server_opts* opts);
+/* Queue one request; ticket receives its id.  Never blocks on the GPU. */
+stmg_status stmg_server_submit(stmg_server_t server, const stmg_request* request, long long* ticket);
+/* Result of a request; wait != 0 blocks until it is done. */
+stmg_status stmg_server_result(stmg_server_t server, long long ticket, int wait, stmg_result* result);
+/* Blocks until every submitted request is done. */
+stmg_status stmg_server_drain(stmg_server_t server);
+double stmg_server_now(stmg_server_t server);
+/* Highest arena use so far, in bytes. */
+long long stmg_server_peak_bytes(stmg_server_t server);
+/* Finishes queued requests, then stops the workers and frees everything. */
+void stmg_server_destroy(stmg_server_t server);
 
 /* ---- statistics ------------------------------------------------------------------------ */
 /* Number of CUDA kernels this library has launched in this process so far (all handles). */

@@ -39,7 +39,24 @@ class Opts(C.Structure):
         ("tol", C.c_double),
         ("div_tol", C.c_double),
         ("max_cycles", C.c_int),
+        ("mixed_first_cycles", C.c_int),
     ]
+
+
+class ServerOpts(C.Structure):
+    _fields_ = [("workers", C.c_int), ("budget_bytes", C.c_longlong), ("cache", C.c_int)]
+
+
+class Request(C.Structure):
+    _fields_ = [("nel", C.c_int), ("nt", C.c_int), ("L", C.c_double), ("t_end", C.c_double),
+                ("k_el", C.c_void_p), ("c_el", C.c_void_p), ("q_el", C.c_void_p), ("q_value", C.c_double),
+                ("adjoint", C.c_int), ("out", C.c_void_p), ("opts", Opts)]
+
+
+class Result(C.Structure):
+    _fields_ = [("status", C.c_int), ("cycles", C.c_int), ("relres", C.c_double), ("theta", C.c_double),
+                ("t_submit", C.c_double), ("t_start", C.c_double), ("t_end", C.c_double), ("bytes", C.c_longlong),
+                ("worker", C.c_int)]
 
 
 _lib = None
@@ -54,6 +71,10 @@ _SIGS = {
     "stmg_last_error": (C.c_char_p, [_vp]),
     "stmg_create": (_i, [C.POINTER(_vp), _i, _i, _d, _d, _vp, _vp, C.POINTER(Opts), _vp]),
     "stmg_update_material": (_i, [_vp, _vp, _vp]),
+    "stmg_create_with_allocator": (_i, [C.POINTER(_vp), _i, _i, _d, _d, _vp, _vp, C.POINTER(Opts), _vp, _vp, _vp,
+                                        _vp]),
+    "stmg_device_bytes": (C.c_longlong, [_vp]),
+    "stmg_footprint": (C.c_longlong, [_i, _i, _d, _d, _vp, _vp, C.POINTER(Opts)]),
     "stmg_destroy": (None, [_vp]),
     "stmg_simp": (_i, [_i, _vp, _dp, _vp, _vp, _vp]),
     "stmg_assemble_load": (_i, [_vp, _vp, _vp]),
@@ -74,6 +95,15 @@ _SIGS = {
     "stmg_vcycle": (_i, [_vp, _i, _vp, _vp]),
     "stmg_sensitivity_noalloc": (_i, [_i, _i, _d, _d, _vp, _dp, _vp, _vp, _vp, _vp]),
     "stmg_kernel_launches": (C.c_ulonglong, []),
+    "stmg_set_stream": (_i, [_vp, _vp]),
+    "stmg_server_default_opts": (None, [C.POINTER(ServerOpts)]),
+    "stmg_server_create": (_i, [C.POINTER(_vp), C.POINTER(ServerOpts)]),
+    "stmg_server_submit": (_i, [_vp, C.POINTER(Request), C.POINTER(C.c_longlong)]),
+    "stmg_server_result": (_i, [_vp, C.c_longlong, _i, C.POINTER(Result)]),
+    "stmg_server_drain": (_i, [_vp]),
+    "stmg_server_now": (_d, [_vp]),
+    "stmg_server_peak_bytes": (C.c_longlong, [_vp]),
+    "stmg_server_destroy": (None, [_vp]),
 }
 
 

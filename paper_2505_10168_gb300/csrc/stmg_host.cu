@@ -7,6 +7,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <unordered_map>
 #include <string>
 #include <utility>
 #include <vector>
@@ -48,7 +49,13 @@ struct stmg_handle {
   std::vector<Level> lev;
   double* partials = nullptr;  // kNormBlocks
   double* scal = nullptr;      // device scalars
-  double* hscal = nullptr;     // pinned host scalars
+  double hscal[8] = {0};       // host copies of device scalars
+  // device memory: cudaMalloc/cudaFree unless the creator supplied hooks
+  stmg_alloc_fn alloc_fn = nullptr;
+  stmg_free_fn free_fn = nullptr;
+  void* actx = nullptr;
+  std::unordered_map<void*, size_t> sizes;  // live allocations (bytes, for stmg_device_bytes)
+  long long bytes = 0;
   double* qstage = nullptr;    // device staging for host element loads
   size_t qstage_n = 0;
   double* sens = nullptr;      // sensitivity scratch
@@ -90,28 +97,48 @@ stmg_status fail(stmg_t h, stmg_status st, const char* fmt, ...) {
     if (st_ != STMG_OK) return st_;       \
   } while (0)
 
+// Allocation sizes are rounded up to 256 bytes (the alignment every hook must provide).
+inline size_t round256(size_t b) { return (b + 255) / 256 * 256; }
+
 template <typename T>
 stmg_status dalloc(stmg_t h, T** p, size_t n) {
   *p = nullptr;
   if (n == 0) n = 1;
-  cudaError_t e = cudaMalloc((void**)p, n * sizeof(T));
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    *p = nullptr;
-    return fail(h, STMG_ENOMEM, "cudaMalloc of %zu bytes failed: %s", n * sizeof(T), cudaGetErrorString(e));
+  const size_t bytes = round256(n * sizeof(T));
+  void* q = nullptr;
+  if (h->alloc_fn) {
+    q = h->alloc_fn(bytes, h->actx);
+    if (!q) return fail(h, STMG_ENOMEM, "allocator hook returned no memory for %zu bytes", bytes);
+  } else {
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(h, STMG_ENOMEM, "cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+    }
   }
+  h->sizes[q] = bytes;
+  h->bytes += (long long)bytes;
+  *p = static_cast<T*>(q);
   return STMG_OK;
 }
 
 template <typename T>
-void dfree(T*& p) {
-  if (p) cudaFree(p);
+void dfree(stmg_t h, T*& p) {
+  if (p) {
+    auto it = h->sizes.find((void*)p);
+    if (it != h->sizes.end()) {
+      h->bytes -= (long long)it->second;
+      h->sizes.erase(it);
+    }
+    if (h->free_fn) h->free_fn((void*)p, h->actx);
+    else cudaFree(p);
+  }
   p = nullptr;
 }
 
-void free_level(Level& L) {
-  dfree(L.dk); dfree(L.dc); dfree(L.cf64); dfree(L.cf32); dfree(L.th);
-  dfree(L.u); dfree(L.b); dfree(L.t); dfree(L.u32); dfree(L.b32); dfree(L.t32);
+void free_level(stmg_t h, Level& L) {
+  dfree(h, L.dk); dfree(h, L.dc); dfree(h, L.cf64); dfree(h, L.cf32); dfree(h, L.th);
+  dfree(h, L.u); dfree(h, L.b); dfree(h, L.t); dfree(h, L.u32); dfree(h, L.b32); dfree(h, L.t32);
 }
 
 bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
@@ -332,6 +359,14 @@ void set_t<double>(Level& L, double* t) { L.t = t; }
 template <>
 void set_t<float>(Level& L, float* t) { L.t32 = t; }
 
+// Exact solve on one level: one thread runs the recurrences for narrow levels, a block-wide
+// scan for wider ones.
+template <typename T>
+cudaError_t exact_level(stmg_t h, const Level& L, bool adj, const T* bs, T* u) {
+  if (L.N > 64) return launch_exact_par<T>(slab_view(L, h->o.omega, L.NT), adj, bs, u, h->s);
+  return launch_exact<T>(thomas_view(L, h->o.omega), adj, bs, u, h->s);
+}
+
 // nsweeps Jacobi steps on level L ping-ponging u and t (the level's u pointer follows
 // the current iterate).
 template <typename T>
@@ -354,7 +389,7 @@ stmg_status vcycle(stmg_t h, int l, bool adj, bool zero_init, bool first_done) {
   Level& L = h->lev[l];
   if (l == (int)h->lev.size() - 1) {
     Vecs<T> v = vecs<T>(L);
-    CK(launch_exact<T>(thomas_view(L, h->o.omega), adj, v.b, v.u, h->s));
+    CK(exact_level<T>(h, L, adj, v.b, v.u));
     return STMG_OK;
   }
   Level& C = h->lev[l + 1];
@@ -413,23 +448,24 @@ StreamArgs stream_args(const Level& L, double omega) {
 // nu > 5), and the prolongation plus the nu post-smoothing sweeps as one UP pass.  On the
 // finest level the result is added to the FP64 iterate u64 (mixed scheme) instead of
 // being stored.  The level's FP32 u pointer ends on the level's result.
-stmg_status vcycle32_fused(stmg_t h, int l, bool adj, double* u64) {
+stmg_status vcycle32_fused(stmg_t h, int l, bool adj, double* u64, bool zero_start = true) {
   Level& L = h->lev[l];
   if (l == (int)h->lev.size() - 1) {
-    CK(launch_exact<float>(thomas_view(L, h->o.omega), adj, L.b32, L.u32, h->s));
+    CK(exact_level<float>(h, L, adj, L.b32, L.u32));
     if (u64) CK(launch_add_correction(L.nvec, u64, L.u32, h->s));
     return STMG_OK;
   }
   Level& C = h->lev[l + 1];
   const std::vector<int> passes = sweep_passes(h->o.nu);
   const bool xc = L.next == STMG_XCOARSEN;
-  // DOWN
-  float* in = nullptr;
-  float* out = L.u32;
+  // DOWN (from zero on coarse levels; on the finest level from the current FP32 iterate
+  // when the cycle continues an inner iteration)
+  float* in = zero_start ? nullptr : L.u32;
+  float* out = zero_start ? L.u32 : L.t32;
   for (size_t p = 0; p < passes.size(); ++p) {
     StreamArgs a = stream_args(L, h->o.omega);
     a.u_in = in;
-    a.zero_init = p == 0;
+    a.zero_init = p == 0 && zero_start;
     a.bs = L.b32;
     a.u_out = out;
     int mode = kStreamPlain;
@@ -508,7 +544,7 @@ stmg_status assemble_into(stmg_t h, const double* q, double* b) {
   if (!is_device_ptr(q)) {
     const size_t n = (size_t)(L.NT + 1) * L.N;
     if (h->qstage_n < n) {
-      dfree(h->qstage);
+      dfree(h, h->qstage);
       h->qstage_n = 0;
       CKS(dalloc(h, &h->qstage, n));
       h->qstage_n = n;
@@ -603,13 +639,25 @@ stmg_status solve_loop(stmg_t h, bool adj, bool warm, int* cycles_out, double* r
   } else if (o.precision == STMG_MIXED) {
     const double nb = std::sqrt(nb2);
     double r2 = nb2;
-    CK(launch_defect(lv, adj, L.u, L.b, L.b32, h->partials, h->scal, h->s));
+    CK(launch_defect(lv, L.cf32, adj, L.u, L.b, L.b32, h->partials, h->scal, h->s));
     CKS(read_scalar(h, h->scal, &r2));
     rel = std::sqrt(r2) / nb;
     if (rel < o.tol) st = STMG_OK;
+    // the first defect is solved by several FP32 cycles (an inner iteration far above the
+    // FP32 rounding floor) before the first FP64 correction
+    const int first = std::max(1, o.mixed_first_cycles);
+    if (st != STMG_OK && first > 1 && o.nu > 0 && o.max_cycles >= first) {
+      for (int j = 1; j <= first; ++j) CKS(vcycle32_fused(h, 0, adj, j == first ? L.u : nullptr, j == 1));
+      CK(launch_defect(lv, L.cf32, adj, L.u, L.b, L.b32, h->partials, h->scal, h->s));
+      CKS(read_scalar(h, h->scal, &r2));
+      rel = std::sqrt(r2) / nb;
+      cycles = first;
+      if (!(rel <= o.div_tol)) st = STMG_EDIVERGED;
+      else if (rel < o.tol) st = STMG_OK;
+    }
     cudaGraphExec_t& gx = h->gexec[1][adj ? 1 : 0];
     unsigned& gk = h->gkernels[1][adj ? 1 : 0];
-    for (int cyc = 1; cyc <= o.max_cycles && st != STMG_OK; ++cyc) {
+    for (int cyc = cycles + 1; cyc <= o.max_cycles && st == STMG_EMAXITER; ++cyc) {
       if (!gx) {
         CKS(capture_graph(h, &gx, &gk, [&]() -> stmg_status {
           if (o.nu > 0) {
@@ -618,7 +666,7 @@ stmg_status solve_loop(stmg_t h, bool adj, bool warm, int* cycles_out, double* r
             CKS(vcycle<float>(h, 0, adj, true, false));
             CK(launch_add_correction(L.nvec, L.u, L.u32, h->s));
           }
-          CK(launch_defect(lv, adj, L.u, L.b, L.b32, h->partials, h->scal, h->s));
+          CK(launch_defect(lv, L.cf32, adj, L.u, L.b, L.b32, h->partials, h->scal, h->s));
           return STMG_OK;
         }));
       }
@@ -694,7 +742,7 @@ stmg_status check_opts(stmg_t h, const stmg_opts& o) {
       (o.reassembly != STMG_REASM_K && o.reassembly != STMG_REASM_R) || o.min_nel < 0 || o.num_levels < 0 ||
       o.num_levels > 60 || o.max_levels < 1 || o.max_levels > 60 || o.max_coarse_dofs < 1 ||
       (o.precision != STMG_FP64 && o.precision != STMG_MIXED) || !(o.tol >= 0) || !(o.div_tol > 0) ||
-      o.max_cycles < 0 || !(o.deff_fixed >= 0))
+      o.max_cycles < 0 || !(o.deff_fixed >= 0) || o.mixed_first_cycles < 0 || o.mixed_first_cycles > 20)
     return fail(h, STMG_EINVAL, "invalid stmg_opts");
   return STMG_OK;
 }
@@ -729,7 +777,7 @@ stmg_status build_hierarchy(stmg_t h, const std::vector<double>& hk, const std::
       std::swap(nl[l].b32, old.b32); std::swap(nl[l].t32, old.t32);
     }
   }
-  for (Level& old : h->lev) free_level(old);
+  for (Level& old : h->lev) free_level(h, old);
   h->lev = std::move(nl);
   for (Level& L : h->lev) CKS(setup_level(h, L));
   CKS(alloc_vectors(h));
@@ -766,12 +814,14 @@ void stmg_default_opts(stmg_opts* o) {
   o->tol = 1e-10;
   o->div_tol = 1e9;
   o->max_cycles = 100;
+  o->mixed_first_cycles = 3;
 }
 
 const char* stmg_last_error(stmg_t h) { return h ? h->err.c_str() : g_global_error.c_str(); }
 
-stmg_status stmg_create(stmg_t* out, int nel, int nt, double L, double t_end, const double* k_el,
-                        const double* c_el, const stmg_opts* opts, void* stream) {
+stmg_status stmg_create_with_allocator(stmg_t* out, int nel, int nt, double L, double t_end, const double* k_el,
+                                       const double* c_el, const stmg_opts* opts, void* stream, stmg_alloc_fn alloc,
+                                       stmg_free_fn free_fn, void* ctx) {
   stmg_t h = nullptr;
   if (!out) return fail(nullptr, STMG_EINVAL, "NULL output handle pointer");
   *out = nullptr;
@@ -779,8 +829,13 @@ stmg_status stmg_create(stmg_t* out, int nel, int nt, double L, double t_end, co
     return fail(nullptr, STMG_EINVAL, "need nel >= 1, nt >= 1, L > 0, t_end > 0");
   if ((long long)(nel + 1) * (long long)(nt + 1) >= (1LL << 31))
     return fail(nullptr, STMG_EINVAL, "grid too large: (nel+1)(nt+1) must stay below 2^31 DOFs");
+  if ((alloc == nullptr) != (free_fn == nullptr))
+    return fail(nullptr, STMG_EINVAL, "give both allocator hooks or neither");
   h = new (std::nothrow) stmg_handle();
   if (!h) return fail(nullptr, STMG_ENOMEM, "host allocation failed");
+  h->alloc_fn = alloc;
+  h->free_fn = free_fn;
+  h->actx = ctx;
   if (opts) h->o = *opts;
   else stmg_default_opts(&h->o);
   h->s = (cudaStream_t)stream;
@@ -790,10 +845,6 @@ stmg_status stmg_create(stmg_t* out, int nel, int nt, double L, double t_end, co
   if (st == STMG_OK) st = read_material(h, nel, k_el, c_el, hk, hc);
   if (st == STMG_OK) st = dalloc(h, &h->partials, kNormBlocks);
   if (st == STMG_OK) st = dalloc(h, &h->scal, 8);
-  if (st == STMG_OK) {
-    cudaError_t e = cudaMallocHost((void**)&h->hscal, 8 * sizeof(double));
-    if (e != cudaSuccess) st = fail(h, STMG_ENOMEM, "cudaMallocHost failed: %s", cudaGetErrorString(e));
-  }
   if (st == STMG_OK) {
     cudaError_t e = cudaStreamCreateWithFlags(&h->cs, cudaStreamNonBlocking);
     if (e != cudaSuccess) st = fail(h, STMG_ECUDA, "cudaStreamCreateWithFlags: %s", cudaGetErrorString(e));
@@ -808,19 +859,54 @@ stmg_status stmg_create(stmg_t* out, int nel, int nt, double L, double t_end, co
   return STMG_OK;
 }
 
+stmg_status stmg_create(stmg_t* out, int nel, int nt, double L, double t_end, const double* k_el,
+                        const double* c_el, const stmg_opts* opts, void* stream) {
+  return stmg_create_with_allocator(out, nel, nt, L, t_end, k_el, c_el, opts, stream, nullptr, nullptr, nullptr);
+}
+
+long long stmg_device_bytes(stmg_t h) { return h ? h->bytes : 0; }
+
+stmg_status stmg_set_stream(stmg_t h, void* stream) {
+  if (!h) return fail(nullptr, STMG_EINVAL, "NULL handle");
+  h->s = (cudaStream_t)stream;  // every call returns with its work complete: nothing is pending
+  return STMG_OK;
+}
+
+long long stmg_footprint(int nel, int nt, double L, double t_end, const double* k_el, const double* c_el,
+                         const stmg_opts* opts) {
+  if (nel < 1 || nt < 1 || !finite_pos(L) || !finite_pos(t_end) || !k_el || !c_el) return -1;
+  if ((long long)(nel + 1) * (long long)(nt + 1) >= (1LL << 31)) return -1;
+  stmg_opts o;
+  if (opts) o = *opts;
+  else stmg_default_opts(&o);
+  for (int e = 0; e < nel; ++e)
+    if (!finite_pos(k_el[e]) || !finite_pos(c_el[e])) return -1;
+  const std::vector<Level> lev = plan_levels(o, nel, nt, L, t_end, k_el, c_el);
+  long long b = (long long)round256(kNormBlocks * sizeof(double)) + (long long)round256(8 * sizeof(double));
+  for (size_t l = 0; l < lev.size(); ++l) {
+    const Level& v = lev[l];
+    b += 2 * (long long)round256(v.N * sizeof(double));
+    b += (long long)round256((size_t)kNumCoef * v.pitch * sizeof(double));
+    b += (long long)round256((size_t)kNumCoef * v.pitch * sizeof(float));
+    b += (long long)round256(8 * (size_t)(v.N + 2) * sizeof(double));
+    if (l == 0 || o.precision == STMG_FP64) b += 3 * (long long)round256(v.nvec * sizeof(double));
+    if (o.precision == STMG_MIXED) b += 3 * (long long)round256(v.nvec * sizeof(float));
+  }
+  return b;
+}
+
 void stmg_destroy(stmg_t h) {
   if (!h) return;
   if (h->s) cudaStreamSynchronize(h->s);
   else cudaDeviceSynchronize();
   reset_graphs(h);
   if (h->cs) cudaStreamDestroy(h->cs);
-  for (Level& L : h->lev) free_level(L);
-  dfree(h->partials);
-  dfree(h->scal);
-  dfree(h->qstage);
-  dfree(h->sens);
-  dfree(h->gstage);
-  if (h->hscal) cudaFreeHost(h->hscal);
+  for (Level& L : h->lev) free_level(h, L);
+  dfree(h, h->partials);
+  dfree(h, h->scal);
+  dfree(h, h->qstage);
+  dfree(h, h->sens);
+  dfree(h, h->gstage);
   delete h;
 }
 
@@ -892,7 +978,7 @@ stmg_status stmg_sensitivity(stmg_t h, const double* chi, const double* simp6, c
   Level& L = h->lev[0];
   const size_t need = 2 * (size_t)sens_chunks(L.NT) * L.N;
   if (h->sens_n < need) {
-    dfree(h->sens);
+    dfree(h, h->sens);
     h->sens_n = 0;
     CKS(dalloc(h, &h->sens, need));
     h->sens_n = need;
@@ -1008,11 +1094,11 @@ stmg_status stmg_exact_solve(stmg_t h, int level, int adjoint, const double* b, 
   CKS(check_level(h, level));
   if (!b || !u) return fail(h, STMG_EINVAL, "NULL array");
   Level& L = h->lev[level];
-  if ((size_t)(L.N + 2) * 16 > 200 * 1024) return fail(h, STMG_EINVAL, "level too wide for the exact solver");
+  if (L.N > 512 * kMaxNodesPerThread) return fail(h, STMG_EINVAL, "level too wide for the exact solver");
   CKS(ensure_fp64(h, L));
   CKS(copy_in(h, L.b, L.pitch, b, L.NT + 1, L.N + 1));
   CK(launch_scale<double>(view<double>(L, h->o.omega), true, L.b, h->s));
-  CK(launch_exact<double>(thomas_view(L, h->o.omega), adjoint != 0, L.b, L.u, h->s));
+  CK(exact_level<double>(h, L, adjoint != 0, L.b, L.u));
   CKS(copy_out(h, u, L.u, L.pitch, L.NT + 1, L.N + 1));
   CK(cudaStreamSynchronize(h->s));
   return STMG_OK;
@@ -1031,7 +1117,7 @@ static stmg_status slabs_common(stmg_t h, const double* b_nodal, const double* c
   *ckpt_dev = ckpt;
   if (!is_device_ptr(ckpt)) {
     if (h->qstage_n < n) {
-      dfree(h->qstage);
+      dfree(h, h->qstage);
       h->qstage_n = 0;
       CKS(dalloc(h, &h->qstage, std::max(n, (size_t)(L.NT + 1) * L.N)));
       h->qstage_n = std::max(n, (size_t)(L.NT + 1) * L.N);
@@ -1064,7 +1150,7 @@ stmg_status stmg_sensitivity_slabs(stmg_t h, const double* chi, const double* si
   const int nslabs = (L.NT + slab_rows - 1) / slab_rows;
   const size_t need = 2 * (size_t)nslabs * L.N;
   if (h->sens_n < need) {
-    dfree(h->sens);
+    dfree(h, h->sens);
     h->sens_n = 0;
     CKS(dalloc(h, &h->sens, need));
     h->sens_n = need;
@@ -1089,7 +1175,7 @@ stmg_status stmg_vcycle(stmg_t h, int adjoint, double* u, const double* b) {
   CKS(copy_in(h, L.b, L.pitch, b, L.NT + 1, L.N + 1));
   CK(launch_scale<double>(view<double>(L, h->o.omega), true, L.b, h->s));
   if (h->o.precision == STMG_MIXED) {
-    CK(launch_defect(view<double>(L, h->o.omega), adjoint != 0, L.u, L.b, L.b32, h->partials, h->scal, h->s));
+    CK(launch_defect(view<double>(L, h->o.omega), L.cf32, adjoint != 0, L.u, L.b, L.b32, h->partials, h->scal, h->s));
     if (h->o.nu > 0) {
       CKS(vcycle32_fused(h, 0, adjoint != 0, L.u));
     } else {
@@ -1107,6 +1193,28 @@ stmg_status stmg_vcycle(stmg_t h, int adjoint, double* u, const double* b) {
 }  // extern "C"
 
 extern "C" unsigned long long stmg_kernel_launches(void) { return launches_so_far(); }
+
+stmg_status stmg_solve_resident(stmg_t h, bool adj, const double* q_dev, double q_value, double rhs_scale, double* out,
+                                int* cycles, double* relres, double* theta) {
+  if (!h) return fail(nullptr, STMG_EINVAL, "NULL handle");
+  Level& L = h->lev[0];
+  const LevelView<double> lv = view<double>(L, h->o.omega);
+  normalize_level0(h);
+  CK(launch_assemble_load(lv, L.dx, q_dev, L.b, h->s, q_value, rhs_scale));
+  stmg_status st = solve_loop(h, adj, false, cycles, relres);
+  if (st != STMG_OK && st != STMG_EDIVERGED && st != STMG_EMAXITER) return st;
+  if (theta) {
+    CK(cudaMemcpyAsync(L.t, L.b, L.nvec * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
+    CK(launch_scale<double>(lv, false, L.t, h->s));
+    CK(launch_dot(L.nvec, L.t, L.u, h->partials, h->scal, h->s));
+    double d = 0.0;
+    CKS(read_scalar(h, h->scal, &d));
+    *theta = d * L.dt / rhs_scale;
+  }
+  if (out) CKS(copy_out(h, out, L.u, L.pitch, L.NT + 1, L.N + 1));
+  CK(cudaStreamSynchronize(h->s));
+  return st;
+}
 
 namespace stmg {
 void set_global_error(const char* msg) { g_global_error = msg; }

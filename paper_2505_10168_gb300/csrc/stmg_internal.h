@@ -29,6 +29,8 @@
 
 #include <cuda_runtime.h>
 
+#include "stmg.h"
+
 namespace stmg {
 
 enum CoefSlot {
@@ -128,9 +130,10 @@ template <typename T>
 cudaError_t launch_resnorm(const LevelView<T>& lv, bool adj, const T* u, const T* bs, double* partials, double* out,
                            cudaStream_t s);
 // Mixed scheme, FP64 level 0: y = (omega/D)(b - J u) stored as FP32 (it is the scaled
-// right-hand side of the FP32 cycle), with ||b - J u||^2 into out[0].
-cudaError_t launch_defect(const LevelView<double>& lv, bool adj, const double* u, const double* bs, float* ys32,
-                          double* partials, double* out, cudaStream_t s);
+// right-hand side of the FP32 cycle), with ||b - J u||^2 (accumulated in FP32 per thread;
+// it only feeds the termination test) into out[0].  coef32: the level's FP32 coefficients.
+cudaError_t launch_defect(const LevelView<double>& lv, const float* coef32, bool adj, const double* u,
+                          const double* bs, float* ys32, double* partials, double* out, cudaStream_t s);
 // u64 += double(e32) over the whole padded array.
 cudaError_t launch_add_correction(size_t n, double* u, const float* e, cudaStream_t s);
 // a . b over the padded arrays (padding is zero) into out[0]; deterministic.
@@ -144,8 +147,10 @@ struct Simp6 {
   double v[6];
 };
 cudaError_t launch_simp(int N, const double* chi, Simp6 sp, double* k, double* c, cudaStream_t s);
-// b' = (omega/D) B b_Neu from element loads q[(NT+1) x N] (dense) into the padded layout.
-cudaError_t launch_assemble_load(const LevelView<double>& lv, double dx, const double* q, double* bs, cudaStream_t s);
+// b' = mult (omega/D) B b_Neu from element loads q[(NT+1) x N] (dense; nullptr: the
+// constant qconst on every element) into the padded layout.
+cudaError_t launch_assemble_load(const LevelView<double>& lv, double dx, const double* q, double* bs, cudaStream_t s,
+                                 double qconst = 0.0, double mult = 1.0);
 // Sensitivity: partial sums over time chunks, then the per-element reduction.
 constexpr int kSensRowsPerChunk = 256;
 // scratch: 2 * sens_chunks(NT) * N doubles.
@@ -158,3 +163,11 @@ cudaError_t launch_sens_final(int N, int chunks, const double* chi, Simp6 sp, co
 inline int sens_chunks(int NT) { return (NT + kSensRowsPerChunk) / kSensRowsPerChunk; }
 
 }  // namespace stmg
+
+// Library-internal entry for the request server (stmg_host.cu): solves on the handle's
+// finest level with the load assembled on the device from q_dev (element loads in device
+// memory) or, when q_dev is null, the uniform load q_value; the right-hand side is
+// multiplied by rhs_scale (dt for the compliance adjoint).  theta = b^T x dt of the result
+// x with b the unscaled load vector; out (host or device, optional) receives x.
+stmg_status stmg_solve_resident(stmg_t h, bool adjoint, const double* q_dev, double q_value, double rhs_scale,
+                                double* out, int* cycles, double* relres, double* theta);

@@ -266,6 +266,30 @@ __global__ void __launch_bounds__(kThreads) k_resnorm(LevelView<T> lv, uint32_t 
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
+// Mixed-scheme defect on the finest level: y = (omega/D)(b - J u) in FP64 (the scaled
+// residual of the FP64 iterate), stored as FP32 as the right-hand side of the next FP32
+// cycle.  The squared norm, which only feeds the termination test, is accumulated in FP32
+// per thread (r = (D/omega) y with the FP32 coefficients) and summed in FP64 across the
+// block: 6 FP64 FMAs and one conversion per DOF.
+template <bool ADJ>
+__global__ void __launch_bounds__(kThreads) k_defect(LevelView<double> lv, uint32_t total, const float* __restrict__ dw32,
+                                                     const double* __restrict__ u, const double* __restrict__ bs,
+                                                     float* __restrict__ ys32, double* __restrict__ partials) {
+  float acc = 0.f;
+  const float Wo32 = (float)lv.Wo;
+  for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+    int n, i;
+    split_index(idx, lv.fd, n, i);
+    const size_t p = (size_t)n * lv.pitch + i;
+    const float y = (float)scaled_residual<double, ADJ>(lv, u, bs, n, i, p);
+    ys32[p] = y;
+    const float r = ((n == 0 || i == 0) ? Wo32 : dw32[i]) * y;
+    acc = fmaf(r, r, acc);
+  }
+  const double s = block_sum<kThreads>((double)acc);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
 __global__ void k_final_sum(const double* __restrict__ partials, int n, double* __restrict__ out) {
   double acc = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) acc += partials[i];
@@ -338,9 +362,11 @@ __global__ void k_simp(int N, const double* __restrict__ chi, Simp6 sp, double* 
 }
 
 // b = B b_Neu with b_Neu,i = dx/2 (q_{i-1} + q_i) for element-wise constant q, stored
-// scaled as b' = (omega/D) b.  Writes every value of the padded rows.
+// scaled as b' = mult (omega/D) b; q == nullptr: the same constant qconst on every element.
+// Writes every value of the padded rows.
 __global__ void __launch_bounds__(kThreads) k_assemble_load(LevelView<double> lv, double dx,
-                                                            const double* __restrict__ q, double* __restrict__ b) {
+                                                            const double* __restrict__ q, double qconst, double mult,
+                                                            double* __restrict__ b) {
   const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long total = (long long)(lv.NT + 1) * lv.pitch;
   if (idx >= total) return;
@@ -349,8 +375,14 @@ __global__ void __launch_bounds__(kThreads) k_assemble_load(LevelView<double> lv
   const int i = (int)(idx - (long long)n * lv.pitch);
   double v = 0.0;
   if (n >= 1 && i >= 1 && i <= N) {
-    const double* qn = q + (size_t)n * N;
-    v = lv.coef[kW * lv.pitch + i] * (0.5 * dx * (qn[i - 1] + (i < N ? qn[i] : 0.0)));
+    double qs;
+    if (q) {
+      const double* qn = q + (size_t)n * N;
+      qs = qn[i - 1] + (i < N ? qn[i] : 0.0);
+    } else {
+      qs = i < N ? 2.0 * qconst : qconst;
+    }
+    v = mult * (lv.coef[kW * lv.pitch + i] * (0.5 * dx * qs));
   }
   b[idx] = v;
 }
@@ -499,11 +531,12 @@ cudaError_t launch_resnorm(const LevelView<T>& lv, bool adj, const T* u, const T
   return cudaGetLastError();
 }
 
-cudaError_t launch_defect(const LevelView<double>& lv, bool adj, const double* u, const double* bs, float* ys32,
-                          double* partials, double* out, cudaStream_t s) {
+cudaError_t launch_defect(const LevelView<double>& lv, const float* coef32, bool adj, const double* u,
+                          const double* bs, float* ys32, double* partials, double* out, cudaStream_t s) {
   const uint32_t n = dofs(lv);
-  if (adj) k_resnorm<double, float, true><<<kNormBlocks, kThreads, 0, s>>>(lv, n, u, bs, ys32, partials);
-  else k_resnorm<double, float, false><<<kNormBlocks, kThreads, 0, s>>>(lv, n, u, bs, ys32, partials);
+  const float* dw32 = coef32 + (size_t)kDW * lv.pitch;
+  if (adj) k_defect<true><<<kNormBlocks, kThreads, 0, s>>>(lv, n, dw32, u, bs, ys32, partials);
+  else k_defect<false><<<kNormBlocks, kThreads, 0, s>>>(lv, n, dw32, u, bs, ys32, partials);
   k_final_sum<<<1, 1024, 0, s>>>(partials, kNormBlocks, out);
   count_launches(2);
   return cudaGetLastError();
@@ -536,8 +569,8 @@ cudaError_t launch_simp(int N, const double* chi, Simp6 sp, double* k, double* c
 }
 
 cudaError_t launch_assemble_load(const LevelView<double>& lv, double dx, const double* q, double* bs,
-                                 cudaStream_t s) {
-  k_assemble_load<<<blocks_for((long long)(lv.NT + 1) * lv.pitch), kThreads, 0, s>>>(lv, dx, q, bs);
+                                 cudaStream_t s, double qconst, double mult) {
+  k_assemble_load<<<blocks_for((long long)(lv.NT + 1) * lv.pitch), kThreads, 0, s>>>(lv, dx, q, qconst, mult, bs);
   count_launches(1);
   return cudaGetLastError();
 }

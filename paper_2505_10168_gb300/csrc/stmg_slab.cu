@@ -162,6 +162,62 @@ __global__ void __launch_bounds__(kSlabThreads) k_slabs(SlabView sv, const doubl
   }
 }
 
+// Exact solve of J u = b (ADJ: J^T u = b) over a whole level in one block: Dirichlet
+// DOFs u = b / W = b' / omega, then each time level from the previous (next for J^T) by
+// the same two block-scanned Thomas recurrences.  T is the storage type; arithmetic and
+// the carried row are FP64.  The coarsest-level solver of Alg. 1 for wide levels.
+template <typename T, bool ADJ>
+__global__ void __launch_bounds__(kSlabThreads) k_exact_par(SlabView sv, const T* __restrict__ bs,
+                                                            T* __restrict__ u) {
+  extern __shared__ double sm[];
+  const int N = sv.N, NT = sv.NT, P = sv.pitch;
+  double* prev = sm;
+  double* cur = sm + (N + 2);
+  double* sh = sm + 2 * (N + 2);
+  for (int i = threadIdx.x; i <= N; i += kSlabThreads) u[i] = (T)((double)bs[i] / sv.omega);
+  for (int n = 1 + threadIdx.x; n <= NT; n += kSlabThreads)
+    u[(size_t)n * P] = (T)((double)bs[(size_t)n * P] / sv.omega);
+  for (int i = threadIdx.x; i <= N + 1; i += kSlabThreads) prev[i] = cur[i] = 0.0;
+  const int per = (N + kSlabThreads - 1) / kSlabThreads;
+  const int i0 = 1 + threadIdx.x * per;
+  const int i1 = min(N, i0 + per - 1);
+  __syncthreads();
+  for (int step = 1; step <= NT; ++step) {
+    const int n = ADJ ? NT + 1 - step : step;
+    const bool has_prev = ADJ ? (n < NT) : (n > 1);
+    const T* bn = bs + (size_t)n * P;
+    Aff loc{1.0, 0.0};
+    for (int i = i0; i <= i1; ++i) {
+      double f = (double)bn[i] * sv.dw[i];
+      if (has_prev) f -= sv.pl[i] * prev[i - 1] + sv.pc[i] * prev[i] + sv.pr[i] * prev[i + 1];
+      cur[i] = f * sv.inv[i];
+      loc = compose(Aff{sv.alpha[i], cur[i]}, loc);
+    }
+    Aff pre = block_exclusive_scan<false>(loc, sh);
+    double y = pre.C;
+    for (int i = i0; i <= i1; ++i) {
+      y = fma(sv.alpha[i], y, cur[i]);
+      cur[i] = y;
+    }
+    __syncthreads();
+    Aff locb{1.0, 0.0};
+    for (int i = i1; i >= i0; --i) locb = compose(Aff{sv.beta[i], cur[i]}, locb);
+    Aff preb = block_exclusive_scan<true>(locb, sh);
+    double x = preb.C;
+    for (int i = i1; i >= i0; --i) {
+      x = fma(sv.beta[i], x, cur[i]);
+      cur[i] = x;
+    }
+    __syncthreads();
+    T* un = u + (size_t)n * P;
+    for (int i = i0; i <= i1; ++i) {
+      un[i] = (T)cur[i];
+      prev[i] = cur[i];
+    }
+    __syncthreads();
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_slabs(const SlabView& sv, const double* bs, const double* ckpt, double* u_out, const double* lam,
@@ -179,5 +235,29 @@ cudaError_t launch_slabs(const SlabView& sv, const double* bs, const double* ckp
   count_launches(1);
   return cudaGetLastError();
 }
+
+}  // namespace stmg
+
+namespace stmg {
+
+template <typename T>
+cudaError_t launch_exact_par(const SlabView& sv, bool adj, const T* bs, T* u, cudaStream_t s) {
+  if ((sv.N + kSlabThreads - 1) / kSlabThreads > kMaxNodesPerThread) return cudaErrorInvalidValue;
+  const size_t smem = sizeof(double) * (2 * (size_t)(sv.N + 2) + 2 * kSlabWarps);
+  if (smem > 48 * 1024) {
+    cudaError_t e = adj ? cudaFuncSetAttribute(k_exact_par<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smem)
+                        : cudaFuncSetAttribute(k_exact_par<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  if (adj) k_exact_par<T, true><<<1, kSlabThreads, smem, s>>>(sv, bs, u);
+  else k_exact_par<T, false><<<1, kSlabThreads, smem, s>>>(sv, bs, u);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_exact_par<double>(const SlabView&, bool, const double*, double*, cudaStream_t);
+template cudaError_t launch_exact_par<float>(const SlabView&, bool, const float*, float*, cudaStream_t);
 
 }  // namespace stmg

@@ -27,4 +27,9 @@ struct SlabView {
 cudaError_t launch_slabs(const SlabView& sv, const double* bs, const double* ckpt, double* u_out, const double* lam,
                          double* scratch, cudaStream_t s);
 
+// Exact solve of one whole level (J u = b, or J^T u = b) from its scaled right-hand side
+// bs, one block: the coarsest-level solver for levels with more than a few dozen nodes.
+template <typename T>
+cudaError_t launch_exact_par(const SlabView& sv, bool adj, const T* bs, T* u, cudaStream_t s);
+
 }  // namespace stmg

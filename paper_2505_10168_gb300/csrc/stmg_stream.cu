@@ -25,6 +25,7 @@ constexpr int kWin = 32 * kVec;            // columns per warp window
 constexpr int kHalo = 8;                   // halo columns on each side
 constexpr int kOwn = kWin - 2 * kHalo;     // 112 columns owned per window
 constexpr int kWarpsPerBlock = 4;
+constexpr int kPF = 3;                     // rows prefetched ahead
 constexpr unsigned kFull = 0xffffffffu;
 
 __device__ __forceinline__ float4 f4zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
@@ -121,34 +122,67 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_stream(StreamArgs a) {
   for (int k = 0; k <= S; ++k) prev[k] = f4zero();
   float4 held = f4zero();  // t-restriction: residual of the first row of a pair
 
-  for (int n = first;; n += step) {
+  // Loads of the next kPF rows are issued before the current row is computed, so every
+  // warp keeps several rows of HBM traffic in flight.
+  const int count = ADJ ? first - last + 1 : last - first + 1;
+  float4 qb[kPF], qu[kPF], qz[kPF];
+  float qz2[kPF];
+  auto load_row = [&](int k, float4& xb, float4& xu, float4& xz, float& xz2) {
+    const bool ok = k < count;
+    const int n = first + k * step;
+    const size_t ro = (size_t)n * P;
+    xb = ld4(a.bs, ro + col, ok && inside);
+    xu = ld4(a.u_in, ro + col, ok && inside && !a.zero_init);
+    xz = f4zero();
+    xz2 = 0.f;
+    if (MODE == 3) {
+      const int ca = col / 2;
+      if (ok && col >= 0 && ca + 1 < a.pc) {
+        const float2 t = __ldg(reinterpret_cast<const float2*>(a.z + (size_t)n * a.pc + ca));
+        xz.x = t.x;
+        xz.y = t.y;
+      }
+      if (ok && lane == 31 && col >= 0 && ca + 2 < a.pc) xz2 = a.z[(size_t)n * a.pc + ca + 2];
+    } else if (MODE == 4) {
+      xz = ld4(a.z, (size_t)(n >> 1) * a.pc + col, ok && inside);
+    }
+  };
+#pragma unroll
+  for (int p = 0; p < kPF; ++p) load_row(p, qb[p], qu[p], qz[p], qz2[p]);
+
+  for (int it = 0; it < count; ++it) {
+    const int n = first + it * step;
     const bool emit = n >= n0 && n < n1;
     const bool dir_row = n == 0;
     const bool has_prev = ADJ ? (n < a.NT) : (n > 1);
     const size_t rowoff = (size_t)n * P;
-    const float4 b = ld4(a.bs, rowoff + col, inside);
+    const float4 b = qb[0];
     float4 cur[S + 1];
-    if (a.zero_init) cur[0] = f4zero();
-    else cur[0] = ld4(a.u_in, rowoff + col, inside);
+    cur[0] = qu[0];
+    const float4 zr = qz[0];
+    const float zr2 = qz2[0];
+#pragma unroll
+    for (int p = 0; p + 1 < kPF; ++p) {
+      qb[p] = qb[p + 1];
+      qu[p] = qu[p + 1];
+      qz[p] = qz[p + 1];
+      qz2[p] = qz2[p + 1];
+    }
+    load_row(it + kPF, qb[kPF - 1], qu[kPF - 1], qz[kPF - 1], qz2[kPF - 1]);
     if (MODE == 3) {
       // x-prolongation: fine 2j <- z_j, fine 2j+1 <- (z_j + z_{j+1}) / 2
-      const int ca = col / 2;  // even
-      const bool zin = col >= 0 && ca + 1 < a.pc;
-      float2 zz = make_float2(0.f, 0.f);
-      if (zin) zz = __ldg(reinterpret_cast<const float2*>(a.z + (size_t)n * a.pc + ca));
-      float z2 = __shfl_down_sync(kFull, zz.x, 1);
-      if (lane == 31) z2 = (col >= 0 && ca + 2 < a.pc) ? a.z[(size_t)n * a.pc + ca + 2] : 0.f;
-      if (col + 0 >= 0 && col + 0 <= a.N) cur[0].x += zz.x;
-      if (col + 1 >= 0 && col + 1 <= a.N) cur[0].y += 0.5f * (zz.x + zz.y);
-      if (col + 2 >= 0 && col + 2 <= a.N) cur[0].z += zz.y;
-      if (col + 3 >= 0 && col + 3 <= a.N) cur[0].w += 0.5f * (zz.y + z2);
+      float z2 = __shfl_down_sync(kFull, zr.x, 1);
+      if (lane == 31) z2 = zr2;
+      if (col + 0 >= 0 && col + 0 <= a.N) cur[0].x += zr.x;
+      if (col + 1 >= 0 && col + 1 <= a.N) cur[0].y += 0.5f * (zr.x + zr.y);
+      if (col + 2 >= 0 && col + 2 <= a.N) cur[0].z += zr.y;
+      if (col + 3 >= 0 && col + 3 <= a.N) cur[0].w += 0.5f * (zr.y + z2);
     } else if (MODE == 4) {
       // causal t-prolongation: fine rows 2m and 2m+1 <- coarse row m
-      const float4 zz = ld4(a.z, (size_t)(n >> 1) * a.pc + col, inside);
-      if (col + 0 <= a.N) cur[0].x += zz.x;
-      if (col + 1 <= a.N) cur[0].y += zz.y;
-      if (col + 2 <= a.N) cur[0].z += zz.z;
-      if (col + 3 <= a.N) cur[0].w += zz.w;
+      if (col + 0 <= a.N) cur[0].x += zr.x;
+      if (col + 1 <= a.N) cur[0].y += zr.y;
+      if (col + 2 <= a.N) cur[0].z += zr.z;
+      if (col + 3 <= a.N) cur[0].w += zr.w;
     }
 #pragma unroll
     for (int k = 1; k <= S; ++k) {
@@ -217,7 +251,6 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_stream(StreamArgs a) {
     }
 #pragma unroll
     for (int k = 0; k <= S; ++k) prev[k] = cur[k];
-    if (n == last) break;
   }
 }
 

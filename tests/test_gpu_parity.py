@@ -158,6 +158,35 @@ def test_fp32_cycle_matches_oracle_cycle(i, adj, nu):
     g.close()
 
 
+@pytest.mark.parametrize("N,NT", [(300, 40), (2000, 16), (65, 7)])
+@pytest.mark.parametrize("adj", [False, True])
+def test_wide_level_exact_solve(N, NT, adj):
+    """Levels wider than 64 nodes use the block-scan time stepping (scan rounding order:
+    1e-10 of max|u|)."""
+    k, c = _rand_material(N + NT, N, contrast=1e4)
+    g, o = _pair(N, NT, 1.0, 0.3, k, c, num_levels=1)
+    b = _rand_vec(12, o.shape(0))
+    ue = np.empty(o.shape(0))
+    g.exact_solve(0, b, ue, adjoint=adj)
+    assert rel(ue, o.exact_level(0, b, adj=adj)) < 1e-10
+    g.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("adj", [False, True])
+def test_cycle_with_wide_coarsest_level(precision, adj):
+    N, NT = 512, 64
+    k, c = _rand_material(8, N, contrast=1e3)
+    g, o = _pair(N, NT, 1.0, 1.0, k, c, num_levels=3, precision=precision)
+    assert o.levels[-1]["N"] > 64
+    b = _rand_vec(4, o.shape(0))
+    ug = np.zeros(o.shape(0))
+    g.vcycle(ug, b, adjoint=adj)
+    tol = 1e-11 if precision == "fp64" else 2e-4
+    assert rel(ug, o.vcycle(np.zeros(o.shape(0)), b, adj=adj)) < tol
+    g.close()
+
+
 @pytest.mark.parametrize("reasm", ["R", "K"])
 def test_config1_solve_matches_oracle(reasm):
     w = wl.config1()

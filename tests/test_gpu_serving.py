@@ -1,0 +1,86 @@
+"""GPU: the continuous-batching server.
+
+Each request's result must be the same alone and in a mix (bit-identical here: every
+kernel's launch configuration and reduction order depends only on the request itself);
+admission must keep the arena within its budget; a request that cannot fit even alone is
+refused with enomem while the others complete; results solve their systems to the
+requested tolerance.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2505_10168_gb300 import serving as sv
+from paper_2505_10168_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+OPTS = dict(precision="mixed", tol=1e-8, nu=20, max_cycles=300)
+
+
+def _reqs(n, seed=77):
+    reqs = wl.serving_requests(n=n, seed=seed, nx=(32, 256), nt=(64, 512), rate=1e4)
+    return reqs
+
+
+def _run(reqs, workers, budget=0, cache=True):
+    outs = [np.full((r["NT"] + 1, r["N"] + 1), np.nan) for r in reqs]
+    with sv.Server(workers=workers, budget_bytes=budget, cache=cache) as s:
+        ts = []
+        for r, o in zip(reqs, outs):
+            k, c, _ = wl.request_fields(r)
+            ts.append(s.submit(r["N"], r["NT"], r["L"], r["tT"], k, c, q_value=1.0, adjoint=r["adjoint"], out=o,
+                               **OPTS))
+        res = [s.result(t) for t in ts]
+        peak = s.peak_bytes
+    return outs, res, peak
+
+
+def test_results_identical_alone_and_in_the_mix():
+    reqs = _reqs(12)
+    alone_out, alone_res = [], []
+    for r in reqs:  # one at a time, fresh server, no overlap
+        o, res, _ = _run([r], workers=1, cache=False)
+        alone_out.append(o[0])
+        alone_res.append(res[0])
+    mix_out, mix_res, _ = _run(reqs, workers=4)
+    assert len({x["worker"] for x in mix_res}) > 1  # the mix really overlapped
+    for a, ra, m, rm in zip(alone_out, alone_res, mix_out, mix_res):
+        assert ra["status"] == rm["status"] == "ok"
+        assert ra["cycles"] == rm["cycles"]
+        assert np.array_equal(a, m)
+        assert ra["theta"] == rm["theta"]
+
+
+def test_results_solve_their_systems():
+    reqs = _reqs(6, seed=5)
+    outs, res, _ = _run(reqs, workers=3)
+    for r, o, x in zip(reqs, outs, res):
+        k, c, q = wl.request_fields(r)
+        N, NT = r["N"], r["NT"]
+        b = oracle.assemble_load(N, NT, 1.0 / N, q)
+        if r["adjoint"]:
+            b = b * (1.0 / NT)
+        H = oracle.Hierarchy(N, NT, 1.0, 1.0, k, c, num_levels=1)
+        rel = np.linalg.norm(H.residual(0, o, b, adj=r["adjoint"])) / np.linalg.norm(b)
+        assert x["status"] == "ok" and rel < 1e-8, (r, x, rel)
+        theta = float((b * o).sum()) * (1.0 / NT) / ((1.0 / NT) if r["adjoint"] else 1.0)
+        assert x["theta"] == pytest.approx(theta, rel=1e-9)
+
+
+def test_admission_respects_budget_and_refuses_oversize():
+    reqs = _reqs(8, seed=9)
+    import paper_2505_10168_gb300._binding as B
+    import ctypes as C
+    sizes = []
+    for r in reqs:
+        k, c, _ = wl.request_fields(r)
+        o = B.make_opts(**OPTS)
+        sizes.append(B.lib().stmg_footprint(r["N"], r["NT"], 1.0, 1.0, k.ctypes.data, c.ctypes.data, C.byref(o)))
+    budget = int(2.2 * max(sizes))
+    outs, res, peak = _run(reqs, workers=4, budget=budget, cache=False)
+    assert all(x["status"] == "ok" for x in res)
+    assert peak <= budget
+    big = dict(reqs[0], N=4096, NT=4096)
+    outs, res, _ = _run([reqs[1], big, reqs[2]], workers=2, budget=budget, cache=False)
+    assert [x["status"] for x in res] == ["ok", "enomem", "ok"]
