@@ -55,8 +55,8 @@ typedef enum {
     STMG_EMAXITER = 5   /* max_cycles reached before tol (Sec. 3.1 termination rule) */
 } stmg_status;
 
-enum { STMG_INTERP_CAUSAL = 0 };                            /* Sec. 3.1 / 5.1 "C" */
-enum { STMG_REASM_K = 0, STMG_REASM_R = 1 };                /* Sec. 3.1 "K", Sec. 5.1 "R" */
+enum { STMG_INTERP_CAUSAL = 0, STMG_INTERP_BILINEAR = 1 };  /* Sec. 3.1 / 5.1 "C" and "B" */
+enum { STMG_REASM_K = 0, STMG_REASM_R = 1, STMG_REASM_D = 2 }; /* Sec. 3.1 "K", Sec. 5.1 "R" and "D" */
 enum { STMG_FP64 = 0, STMG_MIXED = 1 };                     /* precision of the V-cycle */
 enum { STMG_COARSEST = 0, STMG_XCOARSEN = 1, STMG_TCOARSEN = 2 };
 
@@ -65,8 +65,10 @@ typedef struct {
     int nu;                    /* [5] pre- and post-smoothing steps of Alg. 1 (paper: 5, and 20 in Sec. 6-7) */
     double omega;              /* [0.5] Jacobi damping (Sec. 3.1) */
     double lambda_crit;        /* [0.25] t-coarsen iff lambda_eff < lambda_crit (Alg. 3; Sec. 5.2 value) */
-    int interp;                /* [STMG_INTERP_CAUSAL] prolongation */
-    int reassembly;            /* [STMG_REASM_R] coarse-level material averaging */
+    int interp;                /* [STMG_INTERP_CAUSAL] prolongation in time: causal (copies forward)
+                                  or bilinear 1/2 [1 2 1] (Sec. 5.1); x always 1/2 [1 2 1] */
+    int reassembly;            /* [STMG_REASM_R] coarse-level material averaging (STMG_REASM_D only
+                                  through stmg_create_design) */
     int min_nel;               /* [0] M of Alg. 4 (t-coarsen when N/2 < M); 0 = Alg. 3 */
     int num_levels;            /* [0] > 0: exactly this many levels N_l */
     int max_levels;            /* [30] cap on N_l when num_levels == 0 */
@@ -117,6 +119,15 @@ long long stmg_device_bytes(stmg_t handle);
  * may add staging buffers.  Returns -1 for invalid arguments. */
 long long stmg_footprint(int nel, int nt, double L, double t_end, const double* k_el, const double* c_el,
                          const stmg_opts* opts);
+
+/* Hierarchy for a design field chi[nel] (host or device) with the SIMP model simp6 =
+ * {k_ins, k_con, c_ins, c_con, p_k, p_c} (host, Sec. 2.1) and D-reassembly (Sec. 5.1):
+ * x-coarsening averages chi over element pairs and re-applies the SIMP model on the coarse
+ * level; opts->reassembly is ignored (D is implied).  The only way to use D-reassembly. */
+stmg_status stmg_create_design(stmg_t* handle, int nel, int nt, double L, double t_end, const double* chi,
+                               const double* simp6, const stmg_opts* opts, void* stream);
+/* Replace the design field of a stmg_create_design handle; re-runs the planner. */
+stmg_status stmg_update_design(stmg_t handle, const double* chi);
 
 /* Replace k and c (same nel); re-runs the planner.  With deff_fixed > 0 the coarsening
  * path, and so every level size, is unchanged (Sec. 7.2); otherwise levels may be

@@ -40,13 +40,19 @@ class Solver:
     precision 'fp64'/'mixed', tol, div_tol, max_cycles).
     """
 
-    def __init__(self, nel, nt, L, t_end, k, c, stream=None, **opts):
+    def __init__(self, nel, nt, L, t_end, k=None, c=None, stream=None, chi=None, simp6=None, **opts):
+        """k, c: element material; or chi + simp6 for a design-field hierarchy (D-reassembly)."""
         self.nel, self.nt, self.L, self.t_end = int(nel), int(nt), float(L), float(t_end)
         self.opts = B.make_opts(**opts)
         self.stream = stream if stream is not None else B.default_stream()
         h = C.c_void_p()
-        st = B.lib().stmg_create(C.byref(h), self.nel, self.nt, self.L, self.t_end, B.ptr(k), B.ptr(c),
-                                 C.byref(self.opts), self.stream)
+        if chi is not None:
+            s6 = (C.c_double * 6)(*[float(v) for v in simp6])
+            st = B.lib().stmg_create_design(C.byref(h), self.nel, self.nt, self.L, self.t_end, B.ptr(chi), s6,
+                                            C.byref(self.opts), self.stream)
+        else:
+            st = B.lib().stmg_create(C.byref(h), self.nel, self.nt, self.L, self.t_end, B.ptr(k), B.ptr(c),
+                                     C.byref(self.opts), self.stream)
         B.check(st)
         self._h = h
 
@@ -83,6 +89,9 @@ class Solver:
     # -- solves ----------------------------------------------------------------------
     def update_material(self, k, c):
         B.check(B.lib().stmg_update_material(self._h, B.ptr(k), B.ptr(c)), self._h)
+
+    def update_design(self, chi):
+        B.check(B.lib().stmg_update_design(self._h, B.ptr(chi)), self._h)
 
     def assemble_load(self, q, b):
         B.check(B.lib().stmg_assemble_load(self._h, B.ptr(q), B.ptr(b)), self._h)

@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(_HERE, "libstmg.so")
 
 STATUS = {0: "ok", 1: "einval", 2: "enomem", 3: "ecuda", 4: "diverged", 5: "max_cycles"}
 FP64, MIXED = 0, 1
-REASM = {"K": 0, "R": 1}
+REASM = {"K": 0, "R": 1, "D": 2}
 
 
 class STMGError(RuntimeError):
@@ -71,6 +71,8 @@ _SIGS = {
     "stmg_last_error": (C.c_char_p, [_vp]),
     "stmg_create": (_i, [C.POINTER(_vp), _i, _i, _d, _d, _vp, _vp, C.POINTER(Opts), _vp]),
     "stmg_update_material": (_i, [_vp, _vp, _vp]),
+    "stmg_create_design": (_i, [C.POINTER(_vp), _i, _i, _d, _d, _vp, _dp, C.POINTER(Opts), _vp]),
+    "stmg_update_design": (_i, [_vp, _vp]),
     "stmg_create_with_allocator": (_i, [C.POINTER(_vp), _i, _i, _d, _d, _vp, _vp, C.POINTER(Opts), _vp, _vp, _vp,
                                         _vp]),
     "stmg_device_bytes": (C.c_longlong, [_vp]),
@@ -168,6 +170,8 @@ def make_opts(**kw):
     for key, val in kw.items():
         if key == "reassembly" and isinstance(val, str):
             val = REASM[val]
+        if key == "interp" and isinstance(val, str):
+            val = {"C": 0, "B": 1}[val]
         if key == "precision" and isinstance(val, str):
             val = {"fp64": FP64, "mixed": MIXED}[val]
         if not hasattr(o, key):

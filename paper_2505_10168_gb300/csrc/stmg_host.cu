@@ -28,6 +28,7 @@ struct Level {
   int N = 0, NT = 0, pitch = 0, next = STMG_COARSEST;
   double dx = 0, dt = 0, W = 0, lam = 0;
   std::vector<double> k, c;  // host copies of the level material
+  std::vector<double> chi;   // design field of the level (D-reassembly only)
   size_t nvec = 0;           // (NT+1) * pitch
   // device
   double* dk = nullptr;      // k, c (N values each)
@@ -55,6 +56,8 @@ struct stmg_handle {
   stmg_free_fn free_fn = nullptr;
   void* actx = nullptr;
   std::unordered_map<void*, size_t> sizes;  // live allocations (bytes, for stmg_device_bytes)
+  std::vector<double> chi;                  // design field (D-reassembly)
+  double simp[6] = {0, 0, 0, 0, 0, 0};
   long long bytes = 0;
   double* qstage = nullptr;    // device staging for host element loads
   size_t qstage_n = 0;
@@ -89,6 +92,12 @@ stmg_status fail(stmg_t h, stmg_status st, const char* fmt, ...) {
       return fail(h, e_ == cudaErrorMemoryAllocation ? STMG_ENOMEM : STMG_ECUDA, "%s: %s (%s:%d)", #call, \
                   cudaGetErrorString(e_), __FILE__, __LINE__);                                   \
     }                                                                                            \
+  } while (0)
+
+#define CKS_NULL(expr)                    \
+  do {                                    \
+    stmg_status st_ = (expr);             \
+    if (st_ != STMG_OK) return st_;       \
   } while (0)
 
 #define CKS(expr)                         \
@@ -169,13 +178,19 @@ double level_wdiri(const Level& L) {
   return cmax * L.dx / L.dt + kmax / L.dx;
 }
 
+// SIMP interpolation (Sec. 2.1) on the host, for the D-reassembly of coarse levels.
+double simp_k(const double* s, double chi) { return s[0] + (s[1] - s[0]) * std::pow(chi, s[4]); }
+double simp_c(const double* s, double chi) { return s[2] + (s[3] - s[2]) * std::pow(chi, s[5]); }
+
 std::vector<Level> plan_levels(const stmg_opts& o, int N, int NT, double Ldom, double tT, const double* k,
-                               const double* c) {
+                               const double* c, const double* chi = nullptr, const double* simp = nullptr) {
   std::vector<Level> out;
   Level f;
   f.N = N; f.NT = NT; f.dx = Ldom / N; f.dt = tT / NT;
   f.k.assign(k, k + N);
   f.c.assign(c, c + N);
+  const bool design = o.reassembly == STMG_REASM_D && chi && simp;
+  if (design) f.chi.assign(chi, chi + N);
   out.push_back(std::move(f));
   const int cap = o.num_levels > 0 ? o.num_levels : std::max(1, o.max_levels);
   while (true) {
@@ -199,8 +214,15 @@ std::vector<Level> plan_levels(const stmg_opts& o, int N, int NT, double Ldom, d
       C.N = L.N / 2; C.NT = L.NT; C.dx = 2.0 * L.dx; C.dt = L.dt;
       C.k.resize(C.N);
       C.c.resize(C.N);
+      if (design) C.chi.resize(C.N);
       for (int e = 0; e < C.N; ++e) {
         const double ka = L.k[2 * e], kb = L.k[2 * e + 1];
+        if (design) {  // Sec. 5.1 "D": average the design field, then the SIMP model
+          C.chi[e] = (L.chi[2 * e] + L.chi[2 * e + 1]) / 2.0;
+          C.k[e] = simp_k(simp, C.chi[e]);
+          C.c[e] = simp_c(simp, C.chi[e]);
+          continue;
+        }
         if (o.reassembly == STMG_REASM_R) {
           const double rho = (1.0 / ka + 1.0 / kb) / 2.0;  // mean thermal resistivity
           C.k[e] = 1.0 / rho;
@@ -213,6 +235,7 @@ std::vector<Level> plan_levels(const stmg_opts& o, int N, int NT, double Ldom, d
       C.N = L.N; C.NT = L.NT / 2; C.dx = L.dx; C.dt = 2.0 * L.dt;
       C.k = L.k;
       C.c = L.c;
+      C.chi = L.chi;
     }
     out.push_back(std::move(C));
   }
@@ -359,6 +382,11 @@ void set_t<double>(Level& L, double* t) { L.t = t; }
 template <>
 void set_t<float>(Level& L, float* t) { L.t32 = t; }
 
+// Transfer kernel type of the coarsening below level L: 1 x, 2 causal t, 3 bilinear t.
+inline int transfer_type(const stmg_opts& o, const Level& L) {
+  return L.next == STMG_TCOARSEN && o.interp == STMG_INTERP_BILINEAR ? 3 : L.next;
+}
+
 // Exact solve on one level: one thread runs the recurrences for narrow levels, a block-wide
 // scan for wider ones.
 template <typename T>
@@ -410,13 +438,13 @@ stmg_status vcycle(stmg_t h, int l, bool adj, bool zero_init, bool first_done) {
     Vecs<T> v = vecs<T>(L);
     Vecs<T> vc = vecs<T>(C);
     CK(launch_residual<T>(view<T>(L, h->o.omega), adj, v.u, v.b, v.t, h->s));
-    CK(launch_restrict<T>(L.next, L.N, L.NT, L.pitch, v.t, view<T>(C, h->o.omega), vc.b, h->s));
+    CK(launch_restrict<T>(transfer_type(h->o, L), L.N, L.NT, L.pitch, v.t, view<T>(C, h->o.omega), vc.b, h->s));
   }
   CKS(vcycle<T>(h, l + 1, adj, true, false));
   {
     Vecs<T> v = vecs<T>(L);
     Vecs<T> vc = vecs<T>(C);
-    CK(launch_prolong_add<T>(L.next, L.N, L.NT, L.pitch, v.u, C.N, C.NT, C.pitch, vc.u, h->s));
+    CK(launch_prolong_add<T>(transfer_type(h->o, L), L.N, L.NT, L.pitch, v.u, C.N, C.NT, C.pitch, vc.u, h->s));
   }
   CKS(smooth_level<T>(h, L, adj, h->o.nu));
   return STMG_OK;
@@ -470,7 +498,7 @@ stmg_status vcycle32_fused(stmg_t h, int l, bool adj, double* u64, bool zero_sta
     a.u_out = out;
     int mode = kStreamPlain;
     if (p + 1 == passes.size()) {
-      mode = xc ? kStreamDownX : kStreamDownT;
+      mode = xc ? kStreamDownX : (h->o.interp == STMG_INTERP_BILINEAR ? kStreamDownTB : kStreamDownT);
       a.pc = C.pitch;
       a.ccoef = C.cf32;
       a.cwW = (float)(h->o.omega / C.W);
@@ -492,7 +520,7 @@ stmg_status vcycle32_fused(stmg_t h, int l, bool adj, double* u64, bool zero_sta
     a.u64 = (last && u64) ? u64 : nullptr;
     int mode = kStreamPlain;
     if (p == 0) {
-      mode = xc ? kStreamUpX : kStreamUpT;
+      mode = xc ? kStreamUpX : (h->o.interp == STMG_INTERP_BILINEAR ? kStreamUpTB : kStreamUpT);
       a.pc = C.pitch;
       a.z = C.u32;
     }
@@ -738,8 +766,8 @@ stmg_status solve_loop(stmg_t h, bool adj, bool warm, int* cycles_out, double* r
 }
 
 stmg_status check_opts(stmg_t h, const stmg_opts& o) {
-  if (o.nu < 0 || !(o.omega > 0) || !std::isfinite(o.lambda_crit) || o.interp != STMG_INTERP_CAUSAL ||
-      (o.reassembly != STMG_REASM_K && o.reassembly != STMG_REASM_R) || o.min_nel < 0 || o.num_levels < 0 ||
+  if (o.nu < 0 || !(o.omega > 0) || !std::isfinite(o.lambda_crit) || (o.interp != STMG_INTERP_CAUSAL && o.interp != STMG_INTERP_BILINEAR) ||
+      (o.reassembly != STMG_REASM_K && o.reassembly != STMG_REASM_R && o.reassembly != STMG_REASM_D) || o.min_nel < 0 || o.num_levels < 0 ||
       o.num_levels > 60 || o.max_levels < 1 || o.max_levels > 60 || o.max_coarse_dofs < 1 ||
       (o.precision != STMG_FP64 && o.precision != STMG_MIXED) || !(o.tol >= 0) || !(o.div_tol > 0) ||
       o.max_cycles < 0 || !(o.deff_fixed >= 0) || o.mixed_first_cycles < 0 || o.mixed_first_cycles > 20)
@@ -766,7 +794,8 @@ stmg_status read_material(stmg_t h, int n, const double* k, const double* c, std
 
 stmg_status build_hierarchy(stmg_t h, const std::vector<double>& hk, const std::vector<double>& hc) {
   reset_graphs(h);
-  std::vector<Level> nl = plan_levels(h->o, h->N, h->NT, h->L, h->tT, hk.data(), hc.data());
+  std::vector<Level> nl = plan_levels(h->o, h->N, h->NT, h->L, h->tT, hk.data(), hc.data(),
+                                      h->chi.empty() ? nullptr : h->chi.data(), h->simp);
   // keep device buffers of levels whose shape is unchanged
   for (size_t l = 0; l < nl.size(); ++l) {
     if (l < h->lev.size() && h->lev[l].N == nl[l].N && h->lev[l].NT == nl[l].NT) {
@@ -819,9 +848,12 @@ void stmg_default_opts(stmg_opts* o) {
 
 const char* stmg_last_error(stmg_t h) { return h ? h->err.c_str() : g_global_error.c_str(); }
 
-stmg_status stmg_create_with_allocator(stmg_t* out, int nel, int nt, double L, double t_end, const double* k_el,
-                                       const double* c_el, const stmg_opts* opts, void* stream, stmg_alloc_fn alloc,
-                                       stmg_free_fn free_fn, void* ctx) {
+// Common body of the create calls; chi/simp are given for D-reassembly (k_el, c_el then
+// hold the SIMP material of chi).
+static stmg_status create_common(stmg_t* out, int nel, int nt, double L, double t_end, const double* k_el,
+                                 const double* c_el, const std::vector<double>* chi, const double* simp,
+                                 const stmg_opts* opts, void* stream, stmg_alloc_fn alloc, stmg_free_fn free_fn,
+                                 void* ctx) {
   stmg_t h = nullptr;
   if (!out) return fail(nullptr, STMG_EINVAL, "NULL output handle pointer");
   *out = nullptr;
@@ -842,6 +874,12 @@ stmg_status stmg_create_with_allocator(stmg_t* out, int nel, int nt, double L, d
   h->N = nel; h->NT = nt; h->L = L; h->tT = t_end;
   std::vector<double> hk, hc;
   stmg_status st = check_opts(h, h->o);
+  if (st == STMG_OK && (h->o.reassembly == STMG_REASM_D) != (chi != nullptr))
+    st = fail(h, STMG_EINVAL, "D-reassembly needs the design field: use stmg_create_design (and only it)");
+  if (st == STMG_OK && chi) {
+    h->chi = *chi;
+    for (int i = 0; i < 6; ++i) h->simp[i] = simp[i];
+  }
   if (st == STMG_OK) st = read_material(h, nel, k_el, c_el, hk, hc);
   if (st == STMG_OK) st = dalloc(h, &h->partials, kNormBlocks);
   if (st == STMG_OK) st = dalloc(h, &h->scal, 8);
@@ -859,9 +897,58 @@ stmg_status stmg_create_with_allocator(stmg_t* out, int nel, int nt, double L, d
   return STMG_OK;
 }
 
+stmg_status stmg_create_with_allocator(stmg_t* out, int nel, int nt, double L, double t_end, const double* k_el,
+                                       const double* c_el, const stmg_opts* opts, void* stream, stmg_alloc_fn alloc,
+                                       stmg_free_fn free_fn, void* ctx) {
+  return create_common(out, nel, nt, L, t_end, k_el, c_el, nullptr, nullptr, opts, stream, alloc, free_fn, ctx);
+}
+
 stmg_status stmg_create(stmg_t* out, int nel, int nt, double L, double t_end, const double* k_el,
                         const double* c_el, const stmg_opts* opts, void* stream) {
-  return stmg_create_with_allocator(out, nel, nt, L, t_end, k_el, c_el, opts, stream, nullptr, nullptr, nullptr);
+  return create_common(out, nel, nt, L, t_end, k_el, c_el, nullptr, nullptr, opts, stream, nullptr, nullptr, nullptr);
+}
+
+// Design field chi (host or device) -> host copy and its SIMP material.
+static stmg_status read_design(stmg_t h, int nel, const double* chi, const double* simp6, std::vector<double>& hx,
+                               std::vector<double>& hk, std::vector<double>& hc) {
+  if (!chi || !simp6) return fail(h, STMG_EINVAL, "NULL design field or SIMP parameters");
+  hx.resize(nel);
+  cudaStream_t s = h ? h->s : nullptr;
+  if (cudaMemcpyAsync(hx.data(), chi, nel * sizeof(double), cudaMemcpyDefault, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return fail(h, STMG_ECUDA, "reading chi failed: %s", cudaGetErrorString(cudaGetLastError()));
+  hk.resize(nel);
+  hc.resize(nel);
+  for (int e = 0; e < nel; ++e) {
+    if (!std::isfinite(hx[e])) return fail(h, STMG_EINVAL, "chi must be finite (element %d)", e);
+    hk[e] = simp_k(simp6, hx[e]);
+    hc[e] = simp_c(simp6, hx[e]);
+  }
+  return STMG_OK;
+}
+
+stmg_status stmg_create_design(stmg_t* out, int nel, int nt, double L, double t_end, const double* chi,
+                               const double* simp6, const stmg_opts* opts, void* stream) {
+  if (!out) return fail(nullptr, STMG_EINVAL, "NULL output handle pointer");
+  *out = nullptr;
+  if (nel < 1) return fail(nullptr, STMG_EINVAL, "need nel >= 1");
+  stmg_opts o;
+  if (opts) o = *opts;
+  else stmg_default_opts(&o);
+  o.reassembly = STMG_REASM_D;
+  std::vector<double> hx, hk, hc;
+  CKS_NULL(read_design(nullptr, nel, chi, simp6, hx, hk, hc));
+  return create_common(out, nel, nt, L, t_end, hk.data(), hc.data(), &hx, simp6, &o, stream, nullptr, nullptr,
+                       nullptr);
+}
+
+stmg_status stmg_update_design(stmg_t h, const double* chi) {
+  if (!h) return fail(nullptr, STMG_EINVAL, "NULL handle");
+  if (h->o.reassembly != STMG_REASM_D) return fail(h, STMG_EINVAL, "handle was not created with a design field");
+  std::vector<double> hx, hk, hc;
+  CKS(read_design(h, h->N, chi, h->simp, hx, hk, hc));
+  h->chi = hx;
+  return build_hierarchy(h, hk, hc);
 }
 
 long long stmg_device_bytes(stmg_t h) { return h ? h->bytes : 0; }
@@ -879,6 +966,7 @@ long long stmg_footprint(int nel, int nt, double L, double t_end, const double* 
   stmg_opts o;
   if (opts) o = *opts;
   else stmg_default_opts(&o);
+  if (o.reassembly == STMG_REASM_D) o.reassembly = STMG_REASM_R;  // same level sizes for the same path
   for (int e = 0; e < nel; ++e)
     if (!finite_pos(k_el[e]) || !finite_pos(c_el[e])) return -1;
   const std::vector<Level> lev = plan_levels(o, nel, nt, L, t_end, k_el, c_el);
@@ -1067,7 +1155,8 @@ stmg_status stmg_restrict(stmg_t h, int level, const double* r, double* bc) {
   CKS(ensure_fp64(h, L));
   CKS(ensure_fp64(h, C));
   CKS(copy_in(h, L.t, L.pitch, r, L.NT + 1, L.N + 1));
-  CK(launch_restrict<double>(L.next, L.N, L.NT, L.pitch, L.t, view<double>(C, h->o.omega), C.b, h->s));
+  CK(launch_restrict<double>(transfer_type(h->o, L), L.N, L.NT, L.pitch, L.t, view<double>(C, h->o.omega), C.b,
+                             h->s));
   CK(launch_scale<double>(view<double>(C, h->o.omega), false, C.b, h->s));
   CKS(copy_out(h, bc, C.b, C.pitch, C.NT + 1, C.N + 1));
   CK(cudaStreamSynchronize(h->s));
@@ -1084,7 +1173,8 @@ stmg_status stmg_prolong_add(stmg_t h, int level, const double* z, double* u) {
   CKS(ensure_fp64(h, C));
   CKS(copy_in(h, C.u, C.pitch, z, C.NT + 1, C.N + 1));
   CKS(copy_in(h, L.u, L.pitch, u, L.NT + 1, L.N + 1));
-  CK(launch_prolong_add<double>(L.next, L.N, L.NT, L.pitch, L.u, C.N, C.NT, C.pitch, C.u, h->s));
+  CK(launch_prolong_add<double>(transfer_type(h->o, L), L.N, L.NT, L.pitch, L.u, C.N, C.NT, C.pitch, C.u,
+                                h->s));
   CKS(copy_out(h, u, L.u, L.pitch, L.NT + 1, L.N + 1));
   CK(cudaStreamSynchronize(h->s));
   return STMG_OK;

@@ -87,6 +87,29 @@ struct ThomasView {
   double W, omega;
 };
 
+// FP64 <-> FP32 conversions by IEEE-754 bit fields on the integer pipe (on this GPU the
+// conversion instructions share the slow FP64 pipe).  Magnitudes below 2^-126 become
+// signed zero; the mixed scheme's values are far from both ends of the FP32 range.
+// to_f32_trunc truncates the mantissa (relative error < 2^-23); to_f64 is exact.
+__device__ __forceinline__ float to_f32_trunc(double d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const unsigned sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
+  const unsigned mant = ((hi & 0xfffffu) << 3) | (lo >> 29);
+  unsigned r = sign | ((unsigned)e << 23) | mant;
+  r = e <= 0 ? sign : r;
+  r = e >= 255 ? (sign | 0x7f800000u) : r;
+  return __uint_as_float(r);
+}
+__device__ __forceinline__ double to_f64(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned sign = b & 0x80000000u, e = (b >> 23) & 0xffu, m = b & 0x7fffffu;
+  const unsigned hi = e == 0 ? sign : (sign | ((e + 1023u - 127u) << 20) | (m >> 3));
+  const unsigned lo = e == 0 ? 0u : (m << 29);
+  return __hiloint2double((int)hi, (int)lo);
+}
+
 // Sets the message returned by stmg_last_error(NULL) on this host thread.
 void set_global_error(const char* msg);
 

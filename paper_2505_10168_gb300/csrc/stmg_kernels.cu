@@ -145,8 +145,9 @@ __global__ void __launch_bounds__(kThreads) k_residual(LevelView<T> lv, uint32_t
 }
 
 // Restriction b_c = s P^T r (Sec. 3.1), stored scaled by omega / D_c of the coarse level:
-// x: 1/2 [1 2 1] within the row, s = 1; t (causal): rows 2m and 2m+1, s = 1/2 (row 2m+1
-// absent past the last fine row).
+// type 1, x: 1/2 [1 2 1] within the row, s = 1; type 2, t causal: rows 2m and 2m+1, s = 1/2
+// (row 2m+1 absent past the last fine row); type 3, t bilinear (Sec. 5.1): rows 2m-1, 2m,
+// 2m+1 weighted 1/2, 1, 1/2, s = 1/2.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_restrict(int type, int Nf, int NTf, int pf, const T* __restrict__ r,
                                                        LevelView<T> cv, uint32_t total, T* __restrict__ bc) {
@@ -160,17 +161,24 @@ __global__ void __launch_bounds__(kThreads) k_restrict(int type, int Nf, int NTf
     acc = row[2 * j];
     if (2 * j - 1 >= 0) acc += T(0.5) * row[2 * j - 1];
     if (2 * j + 1 <= Nf) acc += T(0.5) * row[2 * j + 1];
-  } else {
+  } else if (type == 2) {
     acc = r[(size_t)(2 * m) * pf + j];
     if (2 * m + 1 <= NTf) acc += r[(size_t)(2 * m + 1) * pf + j];
+    acc *= T(0.5);
+  } else {
+    // bilinear in time (Sec. 5.1): P^T gathers rows 2m-1, 2m, 2m+1 with 1/2, 1, 1/2; s = 1/2
+    acc = r[(size_t)(2 * m) * pf + j];
+    if (2 * m - 1 >= 0) acc += T(0.5) * r[(size_t)(2 * m - 1) * pf + j];
+    if (2 * m + 1 <= NTf) acc += T(0.5) * r[(size_t)(2 * m + 1) * pf + j];
     acc *= T(0.5);
   }
   const T sc = (m == 0 || j == 0) ? cv.wW : cv.coef[kW * cv.pitch + j];
   bc[(size_t)m * cv.pitch + j] = sc * acc;
 }
 
-// u += P z (Sec. 3.1): x: fine node 2j gets z_j, node 2j+1 gets (z_j + z_{j+1}) / 2;
-// t (causal): fine rows 2m and 2m+1 get coarse row m.
+// u += P z (Sec. 3.1): type 1, x: fine node 2j gets z_j, node 2j+1 gets (z_j + z_{j+1}) / 2;
+// type 2, t causal: fine rows 2m and 2m+1 get coarse row m; type 3, t bilinear: fine row
+// 2m gets z_m and row 2m+1 gets (z_m + z_{m+1}) / 2.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_prolong_add(int type, FastDiv fdf, uint32_t total, int pf,
                                                           T* __restrict__ u, int pc, const T* __restrict__ z) {
@@ -182,8 +190,11 @@ __global__ void __launch_bounds__(kThreads) k_prolong_add(int type, FastDiv fdf,
   if (type == 1) {
     const T* zr = z + (size_t)n * pc;
     add = (i & 1) ? T(0.5) * (zr[i >> 1] + zr[(i >> 1) + 1]) : zr[i >> 1];
-  } else {
+  } else if (type == 2 || !(n & 1)) {
     add = z[(size_t)(n >> 1) * pc + i];
+  } else {
+    // bilinear in time: fine row 2m+1 <- (z_m + z_{m+1}) / 2
+    add = T(0.5) * (z[(size_t)(n >> 1) * pc + i] + z[(size_t)((n >> 1) + 1) * pc + i]);
   }
   u[(size_t)n * pf + i] += add;
 }
@@ -270,7 +281,7 @@ __global__ void __launch_bounds__(kThreads) k_resnorm(LevelView<T> lv, uint32_t 
 // residual of the FP64 iterate), stored as FP32 as the right-hand side of the next FP32
 // cycle.  The squared norm, which only feeds the termination test, is accumulated in FP32
 // per thread (r = (D/omega) y with the FP32 coefficients) and summed in FP64 across the
-// block: 6 FP64 FMAs and one conversion per DOF.
+// block: 6 FP64 FMAs per DOF (the conversion to FP32 runs on the integer pipe).
 template <bool ADJ>
 __global__ void __launch_bounds__(kThreads) k_defect(LevelView<double> lv, uint32_t total, const float* __restrict__ dw32,
                                                      const double* __restrict__ u, const double* __restrict__ bs,
@@ -281,7 +292,7 @@ __global__ void __launch_bounds__(kThreads) k_defect(LevelView<double> lv, uint3
     int n, i;
     split_index(idx, lv.fd, n, i);
     const size_t p = (size_t)n * lv.pitch + i;
-    const float y = (float)scaled_residual<double, ADJ>(lv, u, bs, n, i, p);
+    const float y = to_f32_trunc(scaled_residual<double, ADJ>(lv, u, bs, n, i, p));
     ys32[p] = y;
     const float r = ((n == 0 || i == 0) ? Wo32 : dw32[i]) * y;
     acc = fmaf(r, r, acc);

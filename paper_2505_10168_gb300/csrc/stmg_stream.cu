@@ -38,13 +38,13 @@ __device__ __forceinline__ float4 ld4(const float* __restrict__ p, size_t off, b
 // a = 1 - omega for a sweep and a = -omega for the scaled residual.
 __device__ __forceinline__ float4 stage(float a, const float4& x, const float4& px, const float4& b, bool dir_row,
                                         bool has_prev, const float4& sl, const float4& su, const float4& spl,
-                                        const float4& spc, const float4& spr, int lane) {
-  float xl = __shfl_up_sync(kFull, x.w, 1);
-  float xr = __shfl_down_sync(kFull, x.x, 1);
-  float pl = __shfl_up_sync(kFull, px.w, 1);
-  float pr = __shfl_down_sync(kFull, px.x, 1);
-  if (lane == 0) xl = pl = 0.f;
-  if (lane == 31) xr = pr = 0.f;
+                                        const float4& spc, const float4& spr) {
+  // At the window edges (lanes 0 and 31) the shuffles return the lane's own values: those
+  // columns are halo, whose results are never used, and every value stays finite.
+  const float xl = __shfl_up_sync(kFull, x.w, 1);
+  const float xr = __shfl_down_sync(kFull, x.x, 1);
+  const float pl = __shfl_up_sync(kFull, px.w, 1);
+  const float pr = __shfl_down_sync(kFull, px.x, 1);
   float4 o;
   o.x = fmaf(a, x.x, b.x);
   o.y = fmaf(a, x.y, b.y);
@@ -78,7 +78,8 @@ __device__ __forceinline__ float4 stage(float a, const float4& x, const float4& 
 }
 
 // MODE: 0 plain sweeps, 1 sweeps + residual + x-restriction, 2 sweeps + residual +
-// t-restriction, 3 x-prolongation + sweeps, 4 t-prolongation + sweeps.
+// causal t-restriction, 3 x-prolongation + sweeps, 4 causal t-prolongation + sweeps,
+// 5 sweeps + residual + bilinear t-restriction, 6 bilinear t-prolongation + sweeps.
 template <bool ADJ, int S, int MODE>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_stream(StreamArgs a) {
   const int lane = threadIdx.x & 31;
@@ -97,7 +98,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_stream(StreamArgs a) {
   const float4 spl = ld4(a.coef, (size_t)kSPL * P + col, inside);
   const float4 spc = ld4(a.coef, (size_t)kSPC * P + col, inside);
   const float4 spr = ld4(a.coef, (size_t)kSPR * P + col, inside);
-  constexpr bool DOWN = MODE == 1 || MODE == 2;
+  constexpr bool DOWN = MODE == 1 || MODE == 2 || MODE == 5;
   float4 dw = f4zero();
   if (DOWN) dw = ld4(a.coef, (size_t)kDW * P + col, inside);
   // coarse scaling of the restricted residual: x: coarse nodes col/2 and col/2 + 1;
@@ -108,26 +109,29 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_stream(StreamArgs a) {
     cwx.x = a.ccoef[(size_t)kW * a.pc + col / 2];
     cwx.y = a.ccoef[(size_t)kW * a.pc + col / 2 + 1];
   }
-  if (MODE == 2) cwt = ld4(a.ccoef, (size_t)kW * a.pc + col, inside);
+  if (MODE == 2 || MODE == 5) cwt = ld4(a.ccoef, (size_t)kW * a.pc + col, inside);
 
   const int n0 = chunk * a.rows;
   const int n1 = min(a.NT + 1, n0 + a.rows);
-  constexpr int WARM = DOWN ? S + 1 : S;
+  // rows before the chunk (after it, for J^T) that make every emitted value exact; the
+  // bilinear restriction of the chunk's first coarse row also needs fine row n0 - 1
+  constexpr int WARM = MODE == 5 ? S + 2 : (DOWN ? S + 1 : S);
   const int first = ADJ ? min(a.NT, n1 - 1 + WARM) : max(0, n0 - WARM);
-  const int last = ADJ ? n0 : n1 - 1;
+  const int last = ADJ ? (MODE == 5 ? max(0, n0 - 1) : n0) : n1 - 1;
   const int step = ADJ ? -1 : 1;
 
   float4 prev[S + 1];
 #pragma unroll
   for (int k = 0; k <= S; ++k) prev[k] = f4zero();
   float4 held = f4zero();  // t-restriction: residual of the first row of a pair
+  float4 r1 = f4zero(), r2 = f4zero();  // bilinear t-restriction: residuals of the last two rows
 
   // Loads of the next kPF rows are issued before the current row is computed, so every
   // warp keeps several rows of HBM traffic in flight.
   const int count = ADJ ? first - last + 1 : last - first + 1;
-  float4 qb[kPF], qu[kPF], qz[kPF];
+  float4 qb[kPF], qu[kPF], qz[kPF], qzb[kPF];
   float qz2[kPF];
-  auto load_row = [&](int k, float4& xb, float4& xu, float4& xz, float& xz2) {
+  auto load_row = [&](int k, float4& xb, float4& xu, float4& xz, float& xz2, float4& xzb) {
     const bool ok = k < count;
     const int n = first + k * step;
     const size_t ro = (size_t)n * P;
@@ -143,32 +147,29 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_stream(StreamArgs a) {
         xz.y = t.y;
       }
       if (ok && lane == 31 && col >= 0 && ca + 2 < a.pc) xz2 = a.z[(size_t)n * a.pc + ca + 2];
-    } else if (MODE == 4) {
+    } else if (MODE == 4 || MODE == 6) {
       xz = ld4(a.z, (size_t)(n >> 1) * a.pc + col, ok && inside);
     }
+    xzb = f4zero();
+    if (MODE == 6) xzb = ld4(a.z, (size_t)((n >> 1) + 1) * a.pc + col, ok && inside && (n & 1));
   };
 #pragma unroll
-  for (int p = 0; p < kPF; ++p) load_row(p, qb[p], qu[p], qz[p], qz2[p]);
+  for (int p = 0; p < kPF; ++p) load_row(p, qb[p], qu[p], qz[p], qz2[p], qzb[p]);
 
-  for (int it = 0; it < count; ++it) {
+  // one row: its loads come from ring slot p, which is then refilled kPF rows ahead
+  auto process = [&](const int it, float4& sb, float4& su_, float4& sz, float& sz2, float4& szb) {
     const int n = first + it * step;
     const bool emit = n >= n0 && n < n1;
     const bool dir_row = n == 0;
     const bool has_prev = ADJ ? (n < a.NT) : (n > 1);
     const size_t rowoff = (size_t)n * P;
-    const float4 b = qb[0];
+    const float4 b = sb;
     float4 cur[S + 1];
-    cur[0] = qu[0];
-    const float4 zr = qz[0];
-    const float zr2 = qz2[0];
-#pragma unroll
-    for (int p = 0; p + 1 < kPF; ++p) {
-      qb[p] = qb[p + 1];
-      qu[p] = qu[p + 1];
-      qz[p] = qz[p + 1];
-      qz2[p] = qz2[p + 1];
-    }
-    load_row(it + kPF, qb[kPF - 1], qu[kPF - 1], qz[kPF - 1], qz2[kPF - 1]);
+    cur[0] = su_;
+    const float4 zr = sz;
+    const float zr2 = sz2;
+    const float4 zrb = szb;
+    load_row(it + kPF, sb, su_, sz, sz2, szb);
     if (MODE == 3) {
       // x-prolongation: fine 2j <- z_j, fine 2j+1 <- (z_j + z_{j+1}) / 2
       float z2 = __shfl_down_sync(kFull, zr.x, 1);
@@ -177,26 +178,30 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_stream(StreamArgs a) {
       if (col + 1 >= 0 && col + 1 <= a.N) cur[0].y += 0.5f * (zr.x + zr.y);
       if (col + 2 >= 0 && col + 2 <= a.N) cur[0].z += zr.y;
       if (col + 3 >= 0 && col + 3 <= a.N) cur[0].w += 0.5f * (zr.y + z2);
-    } else if (MODE == 4) {
-      // causal t-prolongation: fine rows 2m and 2m+1 <- coarse row m
-      if (col + 0 <= a.N) cur[0].x += zr.x;
-      if (col + 1 <= a.N) cur[0].y += zr.y;
-      if (col + 2 <= a.N) cur[0].z += zr.z;
-      if (col + 3 <= a.N) cur[0].w += zr.w;
+    } else if (MODE == 4 || MODE == 6) {
+      // causal t-prolongation: fine rows 2m and 2m+1 <- coarse row m; bilinear: fine row
+      // 2m+1 <- (z_m + z_{m+1}) / 2
+      float4 zz = zr;
+      if (MODE == 6 && (n & 1))
+        zz = make_float4(0.5f * (zr.x + zrb.x), 0.5f * (zr.y + zrb.y), 0.5f * (zr.z + zrb.z), 0.5f * (zr.w + zrb.w));
+      if (col + 0 <= a.N) cur[0].x += zz.x;
+      if (col + 1 <= a.N) cur[0].y += zz.y;
+      if (col + 2 <= a.N) cur[0].z += zz.z;
+      if (col + 3 <= a.N) cur[0].w += zz.w;
     }
 #pragma unroll
     for (int k = 1; k <= S; ++k) {
       if (k == 1 && a.zero_init) cur[1] = b;  // a sweep from zero is exactly b'
-      else cur[k] = stage(a.omc, cur[k - 1], prev[k - 1], b, dir_row, has_prev, sl, su, spl, spc, spr, lane);
+      else cur[k] = stage(a.omc, cur[k - 1], prev[k - 1], b, dir_row, has_prev, sl, su, spl, spc, spr);
     }
     if (emit && owner) {
       if (a.u64) {
         double2* q = reinterpret_cast<double2*>(a.u64 + rowoff + col);
         double2 lo = q[0], hi = q[1];
-        lo.x += (double)cur[S].x;
-        lo.y += (double)cur[S].y;
-        hi.x += (double)cur[S].z;
-        hi.y += (double)cur[S].w;
+        lo.x += to_f64(cur[S].x);
+        lo.y += to_f64(cur[S].y);
+        hi.x += to_f64(cur[S].z);
+        hi.y += to_f64(cur[S].w);
         q[0] = lo;
         q[1] = hi;
       } else {
@@ -205,7 +210,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_stream(StreamArgs a) {
     }
     if (DOWN) {
       // scaled residual y = b' - omega u + sum S_k u_k, r = (D / omega) y
-      const float4 y = stage(-a.omega, cur[S], prev[S], b, dir_row, has_prev, sl, su, spl, spc, spr, lane);
+      const float4 y = stage(-a.omega, cur[S], prev[S], b, dir_row, has_prev, sl, su, spl, spc, spr);
       float4 r;
       if (dir_row) {
         r = make_float4(a.Wo * y.x, a.Wo * y.y, a.Wo * y.z, a.Wo * y.w);
@@ -224,6 +229,40 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_stream(StreamArgs a) {
           if (col <= a.N) out[j0] = s0 * (r.x + 0.5f * (rl + r.y));
           if (col + 2 <= a.N) out[j0 + 1] = s1 * (r.z + 0.5f * (r.y + r.w));
         }
+      } else if (MODE == 5) {
+        // b_c[m] = (r[2m] + (r[2m-1] + r[2m+1]) / 2) / 2 (bilinear P^T with s = 1/2), emitted
+        // when the last of the three rows arrives; r1, r2: the two rows before this one
+        int m = -1;
+        float4 sum = f4zero();
+        if (!ADJ) {
+          if ((n & 1) && n - 1 >= n0 && n - 1 < n1) {
+            m = (n - 1) >> 1;
+            const float4 lo = m >= 1 ? r2 : f4zero();
+            sum = make_float4(r1.x + 0.5f * (lo.x + r.x), r1.y + 0.5f * (lo.y + r.y), r1.z + 0.5f * (lo.z + r.z),
+                              r1.w + 0.5f * (lo.w + r.w));
+          } else if (n == a.NT && !(n & 1) && emit) {
+            m = n >> 1;
+            sum = make_float4(r.x + 0.5f * r1.x, r.y + 0.5f * r1.y, r.z + 0.5f * r1.z, r.w + 0.5f * r1.w);
+          }
+        } else {
+          if ((n & 1) && n + 1 >= n0 && n + 1 < n1) {
+            m = (n + 1) >> 1;
+            const float4 hi = n + 2 <= a.NT ? r2 : f4zero();
+            sum = make_float4(r1.x + 0.5f * (hi.x + r.x), r1.y + 0.5f * (hi.y + r.y), r1.z + 0.5f * (hi.z + r.z),
+                              r1.w + 0.5f * (hi.w + r.w));
+          } else if (n == 0 && emit) {
+            m = 0;
+            sum = make_float4(r.x + 0.5f * r1.x, r.y + 0.5f * r1.y, r.z + 0.5f * r1.z, r.w + 0.5f * r1.w);
+          }
+        }
+        if (m >= 0 && owner) {
+          float4 sc = cwt;
+          if (m == 0) sc = make_float4(a.cwW, a.cwW, a.cwW, a.cwW);
+          *reinterpret_cast<float4*>(a.bc + (size_t)m * a.pc + col) =
+              make_float4(0.5f * sc.x * sum.x, 0.5f * sc.y * sum.y, 0.5f * sc.z * sum.z, 0.5f * sc.w * sum.w);
+        }
+        r2 = r1;
+        r1 = r;
       } else {
         // b_c[m] = (r[2m] + r[2m+1]) / 2 (causal P^T with s = 1/2), scaled by omega / D_c
         const bool second = ADJ ? (n % 2 == 0) : (n % 2 == 1 || n == a.NT);
@@ -251,6 +290,11 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_stream(StreamArgs a) {
     }
 #pragma unroll
     for (int k = 0; k <= S; ++k) prev[k] = cur[k];
+  };
+  for (int it = 0; it < count; it += kPF) {
+#pragma unroll
+    for (int p = 0; p < kPF; ++p)
+      if (it + p < count) process(it + p, qb[p], qu[p], qz[p], qz2[p], qzb[p]);
   }
 }
 
@@ -295,6 +339,10 @@ cudaError_t launch_stream(int mode, bool adj, int S, const StreamArgs& a, cudaSt
     case 7: e = launch_mode<true, 3>(a, S, grid, s); break;
     case 8: e = launch_mode<false, 4>(a, S, grid, s); break;
     case 9: e = launch_mode<true, 4>(a, S, grid, s); break;
+    case 10: e = launch_mode<false, 5>(a, S, grid, s); break;
+    case 11: e = launch_mode<true, 5>(a, S, grid, s); break;
+    case 12: e = launch_mode<false, 6>(a, S, grid, s); break;
+    case 13: e = launch_mode<true, 6>(a, S, grid, s); break;
     default: break;
   }
   count_launches(1);

@@ -4,7 +4,15 @@
 
 namespace stmg {
 
-enum StreamMode { kStreamPlain = 0, kStreamDownX = 1, kStreamDownT = 2, kStreamUpX = 3, kStreamUpT = 4 };
+enum StreamMode {
+  kStreamPlain = 0,
+  kStreamDownX = 1,   // + residual + x-restriction
+  kStreamDownT = 2,   // + residual + causal t-restriction
+  kStreamUpX = 3,     // x-prolongation first
+  kStreamUpT = 4,     // causal t-prolongation first
+  kStreamDownTB = 5,  // + residual + bilinear t-restriction
+  kStreamUpTB = 6     // bilinear t-prolongation first
+};
 
 struct StreamArgs {
   // this level (FP32 arrays in the padded layout of stmg_internal.h)

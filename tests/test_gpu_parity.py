@@ -44,7 +44,8 @@ def _pair(N, NT, L, tT, k, c, **opts):
     """The GPU solver and the oracle hierarchy built with the same options."""
     g = pkg.Solver(N, NT, L, tT, T(k), T(c), **opts)
     okw = {kk: v for kk, v in opts.items() if kk in ("nu", "omega", "lambda_crit", "reassembly", "min_nel",
-                                                      "num_levels", "max_levels", "max_coarse_dofs", "deff_fixed")}
+                                                      "num_levels", "max_levels", "max_coarse_dofs", "deff_fixed",
+                                                      "interp")}
     o = oracle.Hierarchy(N, NT, L, tT, k, c, **okw)
     return g, o
 
@@ -155,6 +156,61 @@ def test_fp32_cycle_matches_oracle_cycle(i, adj, nu):
     g.vcycle(ug, b, adjoint=adj)
     uo = o.vcycle(np.zeros(o.shape(0)), b, adj=adj)
     assert rel(ug, uo) < 2e-4
+    g.close()
+
+
+@pytest.mark.parametrize("i", [1, 2, 3])
+@pytest.mark.parametrize("adj", [False, True])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_bilinear_interpolation_matches_oracle(i, adj, precision):
+    """Bilinear space-time interpolation B (Sec. 5.1) on every t-coarsening."""
+    N, NT, L, tT, k, c = _case(i)
+    g, o = _pair(N, NT, L, tT, k, c, max_coarse_dofs=64, interp="B", precision=precision)
+    assert "t" in o.path()
+    b = _rand_vec(3, o.shape(0))
+    ug, uo = np.zeros(o.shape(0)), np.zeros(o.shape(0))
+    cycles = 3 if precision == "fp64" else 1
+    for _ in range(cycles):
+        g.vcycle(ug, b, adjoint=adj)
+        uo = o.vcycle(uo, b, adj=adj)
+    assert rel(ug, uo) < (1e-11 if precision == "fp64" else 2e-4)
+    if precision == "fp64":
+        l = o.path().index("t")
+        r = _rand_vec(8, o.shape(l))
+        bc = np.empty(o.shape(l + 1))
+        assert rel(g.restrict(l, r, bc), o.restrict(l, r)) < 1e-14
+        z = _rand_vec(9, o.shape(l + 1))
+        uu = _rand_vec(10, o.shape(l))
+        assert rel(g.prolong_add(l, z, uu.copy()), o.prolong_add(l, z, uu)) < 1e-14
+    g.close()
+
+
+@pytest.mark.parametrize("adj", [False, True])
+def test_design_reassembly_matches_oracle(adj):
+    """D-reassembly (Sec. 5.1): coarse chi = pair average, SIMP re-applied per level."""
+    N, NT = 128, 256
+    chi = 0.05 + 0.9 * wl.uniform(61, N)
+    s6 = wl.simp_params(1e-3, 1.0, 0.5, 1.0)
+    k, c = oracle.simp(chi, s6)
+    tT = 3.0 * NT / N ** 2
+    g = pkg.Solver(N, NT, 1.0, tT, chi=T(chi), simp6=s6, max_coarse_dofs=64)
+    o = oracle.Hierarchy(N, NT, 1.0, tT, k, c, chi=chi, simp6=s6, reassembly="D", max_coarse_dofs=64)
+    assert g.path() == o.path() and "x" in g.path()
+    for l in range(o.nlevels):
+        kg, cg = g.level_material(l)
+        np.testing.assert_allclose(kg, o.levels[l]["k"], rtol=1e-14)
+        np.testing.assert_allclose(cg, o.levels[l]["c"], rtol=1e-14)
+    b = _rand_vec(5, o.shape(0))
+    ug, uo = np.zeros(o.shape(0)), np.zeros(o.shape(0))
+    for _ in range(2):
+        g.vcycle(ug, b, adjoint=adj)
+        uo = o.vcycle(uo, b, adj=adj)
+    assert rel(ug, uo) < 1e-11
+    chi2 = np.clip(chi + 0.05, 0.0, 1.0)
+    g.update_design(T(chi2))
+    o2 = oracle.Hierarchy(N, NT, 1.0, tT, *oracle.simp(chi2, s6), chi=chi2, simp6=s6, reassembly="D",
+                          max_coarse_dofs=64)
+    np.testing.assert_allclose(g.level_material(o2.nlevels - 1)[0], o2.levels[-1]["k"], rtol=1e-14)
     g.close()
 
 

@@ -372,3 +372,20 @@ def test_two_grid_crossover_band_problem2():
         res[e] = (_two_grid_factor(N, NT, 1.0, tT, k, c, "x"), _two_grid_factor(N, NT, 1.0, tT, k, c, "t"))
     assert res[lo - 2][1] < res[lo - 2][0]  # below the band: t-coarsening better
     assert res[hi + 2][0] < res[hi + 2][1]  # above the band: x-coarsening better
+
+
+def _factor_problem7(N_l, interp):
+    p = wl.paper_problem(7, tT=10.0)
+    k, c = oracle.simp(p["chi"], p["simp"])
+    H = oracle.Hierarchy(p["N"], p["NT"], p["L"], p["tT"], k, c, num_levels=N_l, interp=interp, reassembly="R")
+    b = oracle.assemble_load(p["N"], p["NT"], p["L"] / p["N"], wl.load_paper(p["N"], p["NT"], p["L"], p["tT"]))
+    _, st, cyc, hist = H.solve(b, tol=1e-9, max_cycles=100)
+    return (hist[-1] / hist[0]) ** (1.0 / cyc)
+
+
+@pytest.mark.slow
+def test_causal_beats_bilinear_on_problem7_deep_hierarchies():
+    """Sec. 5.2: on problem 7 the methods are close for N_l <= 5, and for N_l >= 6 causal
+    interpolation converges noticeably faster than bilinear (CR vs BR here)."""
+    for N_l in (6, 8):
+        assert _factor_problem7(N_l, "C") < _factor_problem7(N_l, "B")
