@@ -389,3 +389,74 @@ def test_causal_beats_bilinear_on_problem7_deep_hierarchies():
     interpolation converges noticeably faster than bilinear (CR vs BR here)."""
     for N_l in (6, 8):
         assert _factor_problem7(N_l, "C") < _factor_problem7(N_l, "B")
+
+
+# ---------------------------------------------------------------------------------------
+# Optimisation loop of Sec. 7 (projected-gradient stand-in for MMA)
+# ---------------------------------------------------------------------------------------
+def _projection_by_qp(y, lo, hi, vol):
+    """Euclidean projection of y onto {lo <= x <= hi, mean(x) <= vol} by a generic QP solver."""
+    from scipy.optimize import minimize
+
+    n = y.size
+    res = minimize(lambda x: 0.5 * np.sum((x - y) ** 2), np.clip(y, lo, hi), jac=lambda x: x - y,
+                   bounds=list(zip(lo, hi)), constraints=[{"type": "ineq", "fun": lambda x: vol - x.mean(),
+                                                            "jac": lambda x: -np.ones(n) / n}],
+                   method="SLSQP", options={"ftol": 1e-15, "maxiter": 500})
+    assert res.success, res.message
+    return res.x
+
+
+@pytest.mark.parametrize("case", range(6))
+def test_design_update_is_the_projection(case):
+    from oracle.optim import design_update
+
+    rng = np.random.default_rng(40 + case)
+    n = 24
+    chi = rng.random(n) if case < 4 else np.full(n, 0.5)
+    g = rng.standard_normal(n) * 10.0 ** rng.uniform(-3, 3)
+    if case == 5:
+        g = -np.abs(g)  # every element wants more material: the volume bound is active
+    vol, move = (0.5, 0.2) if case != 3 else (0.1, 0.05)  # case 3: move limit keeps mean above vol
+    x, mu = design_update(chi, g, vol, move)
+    y = chi - move * g / np.abs(g).max()
+    lo, hi = np.maximum(0, chi - move), np.minimum(1, chi + move)
+    assert np.all(x >= lo) and np.all(x <= hi)
+    free = (x > lo + 1e-12) & (x < hi - 1e-12)
+    np.testing.assert_allclose(x[free], y[free] - mu, rtol=0, atol=1e-14)
+    if case == 3:
+        assert mu == 2.0 and np.array_equal(x, lo)
+        return
+    if mu > 0:
+        assert abs(x.mean() - vol) < 1e-14
+        np.testing.assert_allclose(x, _projection_by_qp(y, lo, hi, vol), rtol=0, atol=1e-7)
+    else:
+        assert x.mean() <= vol
+        np.testing.assert_allclose(x, np.clip(y, lo, hi), rtol=0, atol=1e-15)
+
+
+def test_design_update_special_cases():
+    from oracle.optim import design_update
+
+    chi = np.linspace(0.1, 0.6, 11)
+    x, mu = design_update(chi, np.zeros(11), 0.5, 0.2)  # no gradient, constraint inactive
+    assert mu == 0.0 and np.array_equal(x, chi)
+    x, mu = design_update(np.full(8, 0.5), np.ones(8), 0.5, 0.2)  # uniform gradient: uniform step
+    np.testing.assert_allclose(x, 0.3, rtol=0, atol=0)
+    x, mu = design_update(np.full(8, 0.5), -np.ones(8), 0.5, 0.2)  # uniform step back onto the bound
+    assert abs(mu - 0.2) < 1e-15 and np.allclose(x, 0.5, rtol=0, atol=1e-15)
+
+
+def test_optimisation_loop_descends_on_problem7():
+    """Problem 7's materials and load (Sec. 7.1) on a 32 x 32 grid: the design stays
+    feasible and the compliance falls at every update from the uniform start."""
+    from oracle.optim import optimize
+
+    N = NT = 32
+    p = wl.paper_problem(7, N=N, NT=NT)
+    q = wl.load_paper(N, NT, p["L"], p["tT"])
+    designs, thetas = optimize(N, NT, p["L"], p["tT"], p["simp"], q, iters=12)
+    for x in designs:
+        assert np.all((x >= 0) & (x <= 1)) and x.mean() <= 0.5 + 1e-14
+    assert all(b < a for a, b in zip(thetas, thetas[1:]))
+    assert thetas[-1] < 0.93 * thetas[0]
