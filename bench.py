@@ -45,6 +45,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-variant", action="store_true", help="skip the other-precision solve of the same workload")
+    p.add_argument("--mixed-inner", type=int, default=1, help="FP32 V-cycles per FP64 defect in the mixed scheme")
     p.add_argument("--serving-requests", type=int, default=64,
                    help="requests of the 512-request serving trace to replay (0: skip serving)")
     p.add_argument("--serving-workers", type=int, default=6)
@@ -225,6 +226,11 @@ def whole_job_rate(units_per_rank, world, seconds):
 
 
 # ----------------------------------------------------------------------------- serving
+def precision_opts(args, precision):
+    """Solver options that only the mixed scheme takes."""
+    return {"mixed_inner_cycles": args.mixed_inner} if precision == "mixed" else {}
+
+
 SERVING_OPTS = dict(precision="mixed", tol=TOL, nu=20, max_cycles=300)
 
 
@@ -286,7 +292,7 @@ def main():
     u = torch.empty((NT + 1, N + 1), dtype=torch.float64, device=dev)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    solver = pkg.Solver(N, NT, L, tT, k, c, precision=args.precision, tol=TOL)
+    solver = pkg.Solver(N, NT, L, tT, k, c, precision=args.precision, tol=TOL, **precision_opts(args, args.precision))
     setup_ms = 1e3 * (time.perf_counter() - t0)
     levels, path = solver.num_levels, solver.path()
 
@@ -391,7 +397,7 @@ def main():
     variant = None
     if not args.no_variant:
         other = "mixed" if args.precision == "fp64" else "fp64"
-        s2 = pkg.Solver(N, NT, L, tT, k, c, precision=other, tol=TOL)
+        s2 = pkg.Solver(N, NT, L, tT, k, c, precision=other, tol=TOL, **precision_opts(args, other))
         for _ in range(max(1, args.warmup)):
             s2.solve(u, q=q)
         torch.cuda.synchronize()
@@ -405,7 +411,7 @@ def main():
         variant = {"precision": other, "value": world * dofs / (ms2 * 1e-3), "unit": "DOF/s", "ms_per_step": ms2,
                    "cycles": st2[-1][1], "relres": st2[-1][2],
                    "converged": all(x[0] == "ok" and x[2] < TOL for x in st2),
-                   "dtype": "f64" if other == "fp64" else "f32+f64"}
+                   "dtype": "f64" if other == "fp64" else "f32+f64", **precision_opts(args, other)}
         s2.close()
 
     # ---- serving: continuous batching of the uneven forward/adjoint request trace ----
@@ -426,7 +432,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
             "data": "synthetic",
-            "config": {"workload": w["name"], "N": N, "NT": NT, "dofs": dofs, "precision": args.precision,
+            "config": {"workload": w["name"], "N": N, "NT": NT, "dofs": dofs, "precision": args.precision, **precision_opts(args, args.precision),
                        "tol": TOL, "levels": levels, "path": path, "cycles": cycles,
                        "relres": relres, "converged": ok, "setup_ms": setup_ms,
                        "l2": "no flush: every vector (%d MB) exceeds the 129 MB L2" % (dofs * 8 // 2 ** 20),

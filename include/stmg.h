@@ -82,6 +82,8 @@ typedef struct {
     int max_cycles;            /* [100] cycle limit (Sec. 3.1) */
     int mixed_first_cycles;    /* [3] STMG_MIXED: FP32 V-cycles run on the first defect (an inner
                                   iteration) before the first FP64 correction; each counts as a cycle */
+    int mixed_inner_cycles;    /* [1] STMG_MIXED: FP32 V-cycles run on every later defect (1..8); the
+                                  termination test is then taken every mixed_inner_cycles cycles */
 } stmg_opts;
 
 void stmg_default_opts(stmg_opts* opts);
@@ -187,6 +189,23 @@ stmg_status stmg_sensitivity_slabs(stmg_t handle, const double* chi, const doubl
 
 /* Theta = b^T u dt / theta_ref (Sec. 7.1); theta: host output. */
 stmg_status stmg_objective(stmg_t handle, const double* b, const double* u, double theta_ref, double* theta);
+
+/* ---- optimisation loop (Sec. 7) ------------------------------------------------------ */
+/* One design update of the optimisation loop of Sec. 7.2.  The paper updates the design
+ * with MMA, a third-party optimiser that is not part of the method; this call is the
+ * projected-gradient step that stands in for it:
+ *   y = chi - move * (g / max|g|),
+ *   chi_new = clamp(y - mu, max(0, chi - move), min(1, chi + move)),
+ * with mu >= 0 the smallest shift for which mean(chi_new) <= vol_frac (the volume
+ * constraint of Sec. 7.1 for elements of equal size), found by 64 bisection steps on
+ * [0, 2] in FP64 (mu = 2, every element on its lower bound, when the move limit keeps the
+ * mean above vol_frac).  chi_new is then the Euclidean projection of y onto the box and
+ * volume constraints.  g = dtheta (e.g. from stmg_sensitivity); g = 0 gives the projection
+ * of chi.  chi, dtheta, chi_new: nel doubles of device memory (chi_new may equal chi);
+ * 0 < vol_frac <= 1, 0 < move <= 1; stream may be NULL.  Returns after chi_new is complete;
+ * messages go to stmg_last_error(NULL). */
+stmg_status stmg_design_update(int nel, const double* chi, const double* dtheta, double vol_frac, double move,
+                               double* chi_new, void* stream);
 
 /* ---- hierarchy inspection ------------------------------------------------------------ */
 int stmg_num_levels(stmg_t handle);

@@ -30,6 +30,16 @@ def simp(chi, simp6, k, c, stream=None):
     return k, c
 
 
+def design_update(chi, g, vol_frac, move, out, stream=None):
+    """Projected-gradient design update of the optimisation loop (Sec. 7.2; stand-in for
+    MMA): out = clamp(chi - move g / max|g| - mu, max(0, chi - move), min(1, chi + move))
+    with the volume shift mu >= 0 (``stmg_design_update``).  out may be chi."""
+    st = B.lib().stmg_design_update(B.numel(chi), B.ptr(chi), B.ptr(g), float(vol_frac), float(move), B.ptr(out),
+                                    stream if stream is not None else B.default_stream())
+    B.check(st)
+    return out
+
+
 class Solver:
     """One STMG hierarchy (``stmg_create``) on one CUDA stream.
 

@@ -40,6 +40,7 @@ class Opts(C.Structure):
         ("div_tol", C.c_double),
         ("max_cycles", C.c_int),
         ("mixed_first_cycles", C.c_int),
+        ("mixed_inner_cycles", C.c_int),
     ]
 
 
@@ -79,6 +80,7 @@ _SIGS = {
     "stmg_footprint": (C.c_longlong, [_i, _i, _d, _d, _vp, _vp, C.POINTER(Opts)]),
     "stmg_destroy": (None, [_vp]),
     "stmg_simp": (_i, [_i, _vp, _dp, _vp, _vp, _vp]),
+    "stmg_design_update": (_i, [_i, _vp, _vp, _d, _d, _vp, _vp]),
     "stmg_assemble_load": (_i, [_vp, _vp, _vp]),
     "stmg_solve": (_i, [_vp, _vp, _vp, _vp, _i, _ip, _dp]),
     "stmg_solve_adjoint": (_i, [_vp, _vp, _vp, _i, _ip, _dp]),

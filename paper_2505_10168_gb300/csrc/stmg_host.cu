@@ -467,7 +467,6 @@ StreamArgs stream_args(const Level& L, double omega) {
   a.omc = (float)(1.0 - omega);
   a.Wo = (float)(L.W / omega);
   a.coef = L.cf32;
-  stream_layout(L.N, L.NT, a);
   return a;
 }
 
@@ -685,11 +684,14 @@ stmg_status solve_loop(stmg_t h, bool adj, bool warm, int* cycles_out, double* r
     }
     cudaGraphExec_t& gx = h->gexec[1][adj ? 1 : 0];
     unsigned& gk = h->gkernels[1][adj ? 1 : 0];
-    for (int cyc = cycles + 1; cyc <= o.max_cycles && st == STMG_EMAXITER; ++cyc) {
+    // later defects: mixed_inner_cycles FP32 cycles each (the first from zero, the others
+    // continuing the FP32 iterate), then the FP64 correction and the next defect
+    const int inner = o.nu > 0 ? o.mixed_inner_cycles : 1;
+    while (st == STMG_EMAXITER && cycles + inner <= o.max_cycles) {
       if (!gx) {
         CKS(capture_graph(h, &gx, &gk, [&]() -> stmg_status {
           if (o.nu > 0) {
-            CKS(vcycle32_fused(h, 0, adj, L.u));
+            for (int j = 1; j <= inner; ++j) CKS(vcycle32_fused(h, 0, adj, j == inner ? L.u : nullptr, j == 1));
           } else {
             CKS(vcycle<float>(h, 0, adj, true, false));
             CK(launch_add_correction(L.nvec, L.u, L.u32, h->s));
@@ -702,7 +704,7 @@ stmg_status solve_loop(stmg_t h, bool adj, bool warm, int* cycles_out, double* r
       count_launches(gk);
       CKS(read_scalar(h, h->scal, &r2));
       rel = std::sqrt(r2) / nb;
-      cycles = cyc;
+      cycles += inner;
       if (!(rel <= o.div_tol)) {  // also catches NaN
         st = STMG_EDIVERGED;
         break;
@@ -770,7 +772,8 @@ stmg_status check_opts(stmg_t h, const stmg_opts& o) {
       (o.reassembly != STMG_REASM_K && o.reassembly != STMG_REASM_R && o.reassembly != STMG_REASM_D) || o.min_nel < 0 || o.num_levels < 0 ||
       o.num_levels > 60 || o.max_levels < 1 || o.max_levels > 60 || o.max_coarse_dofs < 1 ||
       (o.precision != STMG_FP64 && o.precision != STMG_MIXED) || !(o.tol >= 0) || !(o.div_tol > 0) ||
-      o.max_cycles < 0 || !(o.deff_fixed >= 0) || o.mixed_first_cycles < 0 || o.mixed_first_cycles > 20)
+      o.max_cycles < 0 || !(o.deff_fixed >= 0) || o.mixed_first_cycles < 0 || o.mixed_first_cycles > 20 ||
+      o.mixed_inner_cycles < 1 || o.mixed_inner_cycles > 8)
     return fail(h, STMG_EINVAL, "invalid stmg_opts");
   return STMG_OK;
 }
@@ -844,6 +847,7 @@ void stmg_default_opts(stmg_opts* o) {
   o->div_tol = 1e9;
   o->max_cycles = 100;
   o->mixed_first_cycles = 3;
+  o->mixed_inner_cycles = 1;
 }
 
 const char* stmg_last_error(stmg_t h) { return h ? h->err.c_str() : g_global_error.c_str(); }
@@ -1011,6 +1015,18 @@ stmg_status stmg_simp(int nel, const double* chi, const double* simp6, double* k
   Simp6 sp;
   for (int i = 0; i < 6; ++i) sp.v[i] = simp6[i];
   CK(launch_simp(nel, chi, sp, k_el, c_el, (cudaStream_t)stream));
+  CK(cudaStreamSynchronize((cudaStream_t)stream));
+  return STMG_OK;
+}
+
+stmg_status stmg_design_update(int nel, const double* chi, const double* dtheta, double vol_frac, double move,
+                               double* chi_new, void* stream) {
+  if (nel < 1 || !chi || !dtheta || !chi_new || !(vol_frac > 0.0 && vol_frac <= 1.0) || !(move > 0.0 && move <= 1.0))
+    return fail(nullptr, STMG_EINVAL, "bad stmg_design_update arguments");
+  if (!is_device_ptr(chi) || !is_device_ptr(dtheta) || !is_device_ptr(chi_new))
+    return fail(nullptr, STMG_EINVAL, "stmg_design_update takes device arrays");
+  stmg_t h = nullptr;  // errors go to stmg_last_error(NULL)
+  CK(launch_design_update(nel, chi, dtheta, vol_frac, move, chi_new, (cudaStream_t)stream));
   CK(cudaStreamSynchronize((cudaStream_t)stream));
   return STMG_OK;
 }

@@ -174,6 +174,9 @@ cudaError_t launch_simp(int N, const double* chi, Simp6 sp, double* k, double* c
 // constant qconst on every element) into the padded layout.
 cudaError_t launch_assemble_load(const LevelView<double>& lv, double dx, const double* q, double* bs, cudaStream_t s,
                                  double qconst = 0.0, double mult = 1.0);
+// Projected-gradient design update of the optimisation loop (one block; out may alias chi).
+cudaError_t launch_design_update(int N, const double* chi, const double* g, double vol, double move, double* out,
+                                 cudaStream_t s);
 // Sensitivity: partial sums over time chunks, then the per-element reduction.
 constexpr int kSensRowsPerChunk = 256;
 // scratch: 2 * sens_chunks(NT) * N doubles.

@@ -216,45 +216,167 @@ __global__ void __launch_bounds__(kThreads) k_scale(LevelView<T> lv, uint32_t to
 // Exact solve of J u = b (or J^T u = b) by implicit time stepping: Dirichlet DOFs
 // u = b / W; then for each step a Thomas solve of (M/dt + K)_int T_n = f_n with
 // f_n = b_n - (coupling to the previous step), forward in time for J and backward for
-// J^T.  Arithmetic in FP64 whatever the storage type.  One block; thread 0 runs the
-// sequential recurrence, the other threads fill the Dirichlet DOFs.
+// J^T.  Arithmetic in FP64 whatever the storage type.  For levels of at most 64 elements:
+// one warp, lane l owning nodes 2l+1 and 2l+2.  Both Thomas sweeps are first-order affine
+// recurrences, x_i = a_i x_{i-1} + c_i (elimination) and y_i = e_i y_{i+1} + d_i (back
+// substitution), evaluated as warp scans of affine maps: the multipliers are the same for
+// every step, so their partial products are formed once, and a step costs one FMA and one
+// shuffle per scan level.  Each lane reads the next step's right-hand side a step ahead.
 // The right-hand side arrives scaled (b' = (omega/D) b): b = (D/omega) b' in the interior
 // and u = b / W = b' / omega on the Dirichlet DOFs.
+constexpr int kExactWarpMaxN = 64;
+
+__device__ __forceinline__ double shfl_up_d(double v, int d) { return __shfl_up_sync(0xffffffffu, v, d); }
+__device__ __forceinline__ double shfl_down_d(double v, int d) { return __shfl_down_sync(0xffffffffu, v, d); }
+
 template <typename T>
-__global__ void k_exact(ThomasView tv, bool adj, const T* __restrict__ b, T* __restrict__ u) {
-  extern __shared__ double sm[];
+__global__ void __launch_bounds__(32) k_exact(ThomasView tv, bool adj, const T* __restrict__ b, T* __restrict__ u) {
   const int N = tv.N, NT = tv.NT, P = tv.pitch;
-  for (int i = threadIdx.x; i <= N; i += blockDim.x) u[i] = (T)((double)b[i] / tv.omega);
-  for (int n = 1 + threadIdx.x; n <= NT; n += blockDim.x)
-    u[(size_t)n * P] = (T)((double)b[(size_t)n * P] / tv.omega);
-  __syncthreads();
-  if (threadIdx.x != 0) return;
-  // FP64 rows: prev (previous step, node 0 = 0 since its column is eliminated) and cur.
-  double* prev = sm;
-  double* cur = sm + (N + 2);
-  for (int i = 0; i <= N + 1; ++i) prev[i] = 0.0;
-  cur[0] = 0.0;
-  cur[N + 1] = 0.0;
-  for (int step = 1; step <= NT; ++step) {
-    const int n = adj ? NT + 1 - step : step;
-    const bool has_prev = adj ? (n < NT) : (n > 1);
-    const T* bn = b + (size_t)n * P;
-    // forward elimination (cur holds the modified right-hand side)
-    double dp = 0.0;
-    for (int i = 1; i <= N; ++i) {
-      double f = (double)bn[i] * tv.dw[i];
-      if (has_prev) f -= tv.pl[i] * prev[i - 1] + tv.pc[i] * prev[i] + tv.pr[i] * prev[i + 1];
-      dp = (f - tv.lo[i] * dp) * tv.inv[i];
-      cur[i] = dp;
-    }
-    // back substitution
-    for (int i = N - 1; i >= 1; --i) cur[i] = cur[i] - tv.cp[i] * cur[i + 1];
-    T* un = u + (size_t)n * P;
-    for (int i = 1; i <= N; ++i) {
-      un[i] = (T)cur[i];
-      prev[i] = cur[i];
+  const int lane = threadIdx.x;
+  for (int i = lane; i <= N; i += 32) u[i] = (T)((double)b[i] / tv.omega);
+  for (int n = 1 + lane; n <= NT; n += 32) u[(size_t)n * P] = (T)((double)b[(size_t)n * P] / tv.omega);
+  const int i0 = 2 * lane + 1, i1 = 2 * lane + 2;
+  const bool h0 = i0 <= N, h1 = i1 <= N;
+  // elimination: dp_i = (f_i - lo_i dp_{i-1}) inv_i, i.e. a_i = -lo_i inv_i, c_i = f_i inv_i;
+  // back substitution: y_i = d_i - cp_i y_{i+1}, i.e. e_i = -cp_i; absent nodes are identities
+  const double inv0 = h0 ? tv.inv[i0] : 0.0, inv1 = h1 ? tv.inv[i1] : 0.0;
+  const double a0 = h0 && i0 > 1 ? -tv.lo[i0] * inv0 : (h0 ? 0.0 : 1.0);
+  const double a1 = h1 ? -tv.lo[i1] * inv1 : 1.0;
+  const double e0 = h0 && i0 < N ? -tv.cp[i0] : (h0 ? 0.0 : 1.0);
+  const double e1 = h1 && i1 < N ? -tv.cp[i1] : (h1 ? 0.0 : 1.0);
+  const double dw0 = h0 ? tv.dw[i0] : 0.0, dw1 = h1 ? tv.dw[i1] : 0.0;
+  const double pl0 = h0 ? tv.pl[i0] : 0.0, pc0 = h0 ? tv.pc[i0] : 0.0, pr0 = h0 ? tv.pr[i0] : 0.0;
+  const double pl1 = h1 ? tv.pl[i1] : 0.0, pc1 = h1 ? tv.pc[i1] : 0.0, pr1 = h1 ? tv.pr[i1] : 0.0;
+  // lane aggregates and the Kogge-Stone multipliers of both scans (step-invariant)
+  const double A = a1 * a0, E = e0 * e1;
+  double Af[5], Eb[5];
+  {
+    double x = A, y = E;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      const int d = 1 << k;
+      const double xu = shfl_up_d(x, d), yd = shfl_down_d(y, d);
+      Af[k] = lane >= d ? x : 0.0;
+      Eb[k] = lane + d < 32 ? y : 0.0;
+      if (lane >= d) x *= xu;
+      if (lane + d < 32) y *= yd;
     }
   }
+  double p0 = 0.0, p1 = 0.0;  // previous step's solution at i0, i1 (node 0: eliminated column)
+  auto load = [&](int step, double& f0, double& f1) {
+    const int n = adj ? NT + 1 - step : step;
+    const T* bn = b + (size_t)n * P;
+    f0 = h0 ? (double)bn[i0] * dw0 : 0.0;
+    f1 = h1 ? (double)bn[i1] * dw1 : 0.0;
+  };
+  double f0 = 0.0, f1 = 0.0;
+  if (NT >= 1) load(1, f0, f1);
+  for (int step = 1; step <= NT; ++step) {
+    double g0 = 0.0, g1 = 0.0;
+    if (step < NT) load(step + 1, g0, g1);
+    const int n = adj ? NT + 1 - step : step;
+    const bool has_prev = adj ? (n < NT) : (n > 1);
+    if (has_prev) {
+      const double pm = shfl_up_d(p1, 1);    // node i0 - 1
+      const double pp = shfl_down_d(p0, 1);  // node i1 + 1
+      const double pmm = lane == 0 ? 0.0 : pm;
+      const double ppp = i1 + 1 <= N ? pp : 0.0;
+      f0 -= pl0 * pmm + pc0 * p0 + pr0 * p1;
+      f1 -= pl1 * p0 + pc1 * p1 + pr1 * ppp;
+    }
+    // elimination scan: lane value = dp at node i1 given dp = 0 before node 1
+    const double c0 = f0 * inv0, c1 = f1 * inv1;
+    double C = a1 * c0 + c1;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      const double cu = shfl_up_d(C, 1 << k);
+      if (lane >= (1 << k)) C = fma(Af[k], cu, C);
+    }
+    const double before = lane == 0 ? 0.0 : shfl_up_d(C, 1);
+    const double d0 = h0 ? a0 * before + c0 : 0.0;
+    const double d1 = h1 ? C : 0.0;
+    // back-substitution scan from node N down: lane value = y at node i0
+    double D = e0 * d1 + d0;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      const double dd = shfl_down_d(D, 1 << k);
+      if (lane + (1 << k) < 32) D = fma(Eb[k], dd, D);
+    }
+    const double after = lane == 31 ? 0.0 : shfl_down_d(D, 1);
+    const double y1 = h1 ? e1 * after + d1 : 0.0;
+    const double y0 = h0 ? D : 0.0;
+    T* un = u + (size_t)n * P;
+    if (h0) un[i0] = (T)y0;
+    if (h1) un[i1] = (T)y1;
+    p0 = y0;
+    p1 = y1;
+    f0 = g0;
+    f1 = g1;
+  }
+}
+
+// One projected-gradient design update, the stand-in for the MMA optimiser of the
+// optimisation loop (Sec. 7.2): y = chi - move * (g / max|g|) and
+// chi_new = clamp(y - mu, max(0, chi - move), min(1, chi + move)), mu >= 0 the smallest
+// shift with mean(chi_new) <= vol (the volume constraint of Sec. 7.1), by 64 bisection
+// steps on [0, 2].  One block of 1024 threads; every reduction is a fixed tree, and y, the
+// bounds and the shift are rounded exactly as written (no FMA contraction).
+constexpr int kDesignThreads = 1024;
+constexpr int kDesignBisection = 64;
+
+template <bool MAX>
+__device__ double block_reduce(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const double w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = MAX ? fmax(v, w) : v + w;
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();  // red is reused by consecutive reductions
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    v = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) {
+      const double w = __shfl_xor_sync(0xffffffffu, v, o);
+      v = MAX ? fmax(v, w) : v + w;
+    }
+    if (lane == 0) red[32] = v;
+  }
+  __syncthreads();
+  return red[32];
+}
+
+__device__ __forceinline__ double design_value(double c, double gi, double gmax, double move, double mu) {
+  const double step = gmax > 0.0 ? gi / gmax : 0.0;
+  const double y = __dsub_rn(c, __dmul_rn(move, step));
+  const double lo = fmax(0.0, __dsub_rn(c, move));
+  const double hi = fmin(1.0, __dadd_rn(c, move));
+  return fmin(fmax(__dsub_rn(y, mu), lo), hi);
+}
+
+__global__ void __launch_bounds__(kDesignThreads) k_design_update(int N, const double* chi, const double* g,
+                                                                 double vol, double move, double* out) {
+  __shared__ double red[33];
+  double m = 0.0;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) m = fmax(m, fabs(g[i]));
+  const double gmax = block_reduce<true>(m, red);
+  auto mean_at = [&](double mu) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) s += design_value(chi[i], g[i], gmax, move, mu);
+    return block_reduce<false>(s, red) / N;
+  };
+  double mu = 0.0;
+  if (mean_at(0.0) > vol) {
+    double a = 0.0, b = 2.0;
+    for (int it = 0; it < kDesignBisection; ++it) {
+      const double mid = 0.5 * (a + b);
+      if (mean_at(mid) > vol) a = mid;
+      else b = mid;
+    }
+    mu = b;
+  }
+  // each element is read and written by the same thread: out may alias chi
+  for (int i = threadIdx.x; i < N; i += blockDim.x) out[i] = design_value(chi[i], g[i], gmax, move, mu);
 }
 
 // ||r||^2 of r = b - J u from the stored b' (u null: r = b), optionally storing the
@@ -513,12 +635,15 @@ cudaError_t launch_prolong_add(int type, int Nf, int NTf, int pf, T* u, int Nc, 
 
 template <typename T>
 cudaError_t launch_exact(const ThomasView& tv, bool adj, const T* b, T* u, cudaStream_t s) {
-  const size_t smem = sizeof(double) * 2 * (size_t)(tv.N + 2);
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_exact<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
-  k_exact<T><<<1, 256, smem, s>>>(tv, adj, b, u);
+  if (tv.N < 1 || tv.N > kExactWarpMaxN) return cudaErrorInvalidValue;
+  k_exact<T><<<1, 32, 0, s>>>(tv, adj, b, u);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_design_update(int N, const double* chi, const double* g, double vol, double move, double* out,
+                                 cudaStream_t s) {
+  k_design_update<<<1, kDesignThreads, 0, s>>>(N, chi, g, vol, move, out);
   count_launches(1);
   return cudaGetLastError();
 }

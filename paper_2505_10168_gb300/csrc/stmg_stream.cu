@@ -11,9 +11,19 @@
 // carries an 8-column halo on each side and a chunk starts S(+1) rows early, so every
 // output value is computed from exact inputs with no block-level synchronisation.
 //
+// A row's inputs (b', the starting iterate, the coarse correction, the FP64 iterate) are
+// staged through a per-warp ring of rows in shared memory, filled by asynchronous copies
+// several rows ahead, so the loads in flight cost no registers.  The row loop has no
+// data-dependent branches: the Dirichlet row 0 is peeled off, rows alternate between two
+// register sets of pipeline state, and every row-dependent choice is a select or a
+// predicated store.
+//
 // HBM traffic per DOF of a level (x-coarsening, zero start): DOWN reads b' and writes u
 // and b'_c (10 B); UP reads u, b', z and writes u (14 B); the finest-level UP of the
 // mixed scheme adds its result straight into the FP64 iterate instead (26 B).
+#include <atomic>
+#include <type_traits>
+
 #include "stmg_internal.h"
 #include "stmg_stream.h"
 
@@ -25,7 +35,7 @@ constexpr int kWin = 32 * kVec;            // columns per warp window
 constexpr int kHalo = 8;                   // halo columns on each side
 constexpr int kOwn = kWin - 2 * kHalo;     // 112 columns owned per window
 constexpr int kWarpsPerBlock = 4;
-constexpr int kPF = 3;                     // rows prefetched ahead
+constexpr int kThreads = 32 * kWarpsPerBlock;
 constexpr unsigned kFull = 0xffffffffu;
 
 __device__ __forceinline__ float4 f4zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
@@ -34,56 +44,111 @@ __device__ __forceinline__ float4 ld4(const float* __restrict__ p, size_t off, b
   return ok ? __ldg(reinterpret_cast<const float4*>(p + off)) : f4zero();
 }
 
+// Asynchronous global -> shared copies of base[off ...]; when ok is false nothing is read
+// (base may then be null) and the destination is filled with zeros (src-size 0).
+// fallback is any valid global address.
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+template <int BYTES, typename T>
+__device__ __forceinline__ void cp_async(void* dst, const T* base, size_t off, const void* fallback, bool ok) {
+  const void* src = ok ? static_cast<const void*>(base + off) : fallback;
+  if (BYTES == 16) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32(dst)), "l"(src), "r"(ok ? 16 : 0)
+                 : "memory");
+  } else {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(smem_u32(dst)), "l"(src), "n"(BYTES),
+                 "r"(ok ? BYTES : 0)
+                 : "memory");
+  }
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
 // One stage of the pipeline on a lane's 4 columns: out = a*x + b' + sum_k S_k x_k, with
-// a = 1 - omega for a sweep and a = -omega for the scaled residual.
-__device__ __forceinline__ float4 stage(float a, const float4& x, const float4& px, const float4& b, bool dir_row,
-                                        bool has_prev, const float4& sl, const float4& su, const float4& spl,
-                                        const float4& spc, const float4& spr) {
+// a = 1 - omega for a sweep and a = -omega for the scaled residual.  DIR: a Dirichlet row
+// (time level 0), whose row of J is W_Diri I.  px is the stage input of the previous row
+// (the next row for J^T); it is zero where the stencil has no such coupling.
+template <bool DIR>
+__device__ __forceinline__ float4 stage(float a, const float4& x, const float4& px, const float4& b, const float4& sl,
+                                        const float4& su, const float4& spl, const float4& spc, const float4& spr) {
+  float4 o;
+  o.x = fmaf(a, x.x, b.x);
+  o.y = fmaf(a, x.y, b.y);
+  o.z = fmaf(a, x.z, b.z);
+  o.w = fmaf(a, x.w, b.w);
+  if (DIR) return o;
   // At the window edges (lanes 0 and 31) the shuffles return the lane's own values: those
   // columns are halo, whose results are never used, and every value stays finite.
   const float xl = __shfl_up_sync(kFull, x.w, 1);
   const float xr = __shfl_down_sync(kFull, x.x, 1);
   const float pl = __shfl_up_sync(kFull, px.w, 1);
   const float pr = __shfl_down_sync(kFull, px.x, 1);
-  float4 o;
-  o.x = fmaf(a, x.x, b.x);
-  o.y = fmaf(a, x.y, b.y);
-  o.z = fmaf(a, x.z, b.z);
-  o.w = fmaf(a, x.w, b.w);
-  if (!dir_row) {
-    o.x = fmaf(sl.x, xl, o.x);
-    o.x = fmaf(su.x, x.y, o.x);
-    o.y = fmaf(sl.y, x.x, o.y);
-    o.y = fmaf(su.y, x.z, o.y);
-    o.z = fmaf(sl.z, x.y, o.z);
-    o.z = fmaf(su.z, x.w, o.z);
-    o.w = fmaf(sl.w, x.z, o.w);
-    o.w = fmaf(su.w, xr, o.w);
-    if (has_prev) {
-      o.x = fmaf(spl.x, pl, o.x);
-      o.x = fmaf(spc.x, px.x, o.x);
-      o.x = fmaf(spr.x, px.y, o.x);
-      o.y = fmaf(spl.y, px.x, o.y);
-      o.y = fmaf(spc.y, px.y, o.y);
-      o.y = fmaf(spr.y, px.z, o.y);
-      o.z = fmaf(spl.z, px.y, o.z);
-      o.z = fmaf(spc.z, px.z, o.z);
-      o.z = fmaf(spr.z, px.w, o.z);
-      o.w = fmaf(spl.w, px.z, o.w);
-      o.w = fmaf(spc.w, px.w, o.w);
-      o.w = fmaf(spr.w, pr, o.w);
-    }
-  }
+  o.x = fmaf(sl.x, xl, o.x);
+  o.x = fmaf(su.x, x.y, o.x);
+  o.y = fmaf(sl.y, x.x, o.y);
+  o.y = fmaf(su.y, x.z, o.y);
+  o.z = fmaf(sl.z, x.y, o.z);
+  o.z = fmaf(su.z, x.w, o.z);
+  o.w = fmaf(sl.w, x.z, o.w);
+  o.w = fmaf(su.w, xr, o.w);
+  o.x = fmaf(spl.x, pl, o.x);
+  o.x = fmaf(spc.x, px.x, o.x);
+  o.x = fmaf(spr.x, px.y, o.x);
+  o.y = fmaf(spl.y, px.x, o.y);
+  o.y = fmaf(spc.y, px.y, o.y);
+  o.y = fmaf(spr.y, px.z, o.y);
+  o.z = fmaf(spl.z, px.y, o.z);
+  o.z = fmaf(spc.z, px.z, o.z);
+  o.z = fmaf(spr.z, px.w, o.z);
+  o.w = fmaf(spl.w, px.z, o.w);
+  o.w = fmaf(spc.w, px.w, o.w);
+  o.w = fmaf(spr.w, pr, o.w);
   return o;
 }
+
+__device__ __forceinline__ float4 mul4(const float4& s, const float4& v) {
+  return make_float4(s.x * v.x, s.y * v.y, s.z * v.z, s.w * v.w);
+}
+__device__ __forceinline__ float4 sel4(bool c, const float4& p, const float4& q) {
+  return make_float4(c ? p.x : q.x, c ? p.y : q.y, c ? p.z : q.z, c ? p.w : q.w);
+}
+
+// Fields of one ring slot, 16 bytes per lane each: b', the starting iterate, the coarse
+// correction rows (UP), the FP64 iterate (two fields; UP and plain passes).
+template <int MODE>
+struct Ring {
+  static constexpr bool kDown = MODE == 1 || MODE == 2 || MODE == 5;
+  static constexpr bool kHasZ = MODE == 3 || MODE == 4 || MODE == 6;
+  static constexpr int kB = 0, kU = 1, kZ = 2, kZB = 3;
+  static constexpr int k64 = kDown ? 0 : (MODE == 6 ? 4 : (kHasZ ? 3 : 2));
+  static constexpr int kFields = kDown ? 2 : k64 + 2;
+  static constexpr int kDepth = kDown ? 6 : 4;  // rows in flight per warp
+};
+
+// Pipeline state after one row: v[0] the row's starting iterate (plus the prolongated
+// correction), v[k] the row after sweep k; r, rp the residuals of this row and the one
+// before it (restriction modes).
+template <int S>
+struct Pipe {
+  float4 v[S + 1];
+  float4 r, rp;
+};
 
 // MODE: 0 plain sweeps, 1 sweeps + residual + x-restriction, 2 sweeps + residual +
 // causal t-restriction, 3 x-prolongation + sweeps, 4 causal t-prolongation + sweeps,
 // 5 sweeps + residual + bilinear t-restriction, 6 bilinear t-prolongation + sweeps.
 template <bool ADJ, int S, int MODE>
-__global__ void __launch_bounds__(32 * kWarpsPerBlock) k_stream(StreamArgs a) {
+__global__ void __launch_bounds__(kThreads, 4) k_stream(StreamArgs a) {
+  using R = Ring<MODE>;
+  constexpr bool DOWN = R::kDown;
+  constexpr int kD = R::kDepth;
+  __shared__ float4 ring[kWarpsPerBlock][kD][R::kFields][32];
+
   const int lane = threadIdx.x & 31;
-  const int wid = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  const int w = threadIdx.x >> 5;
+  const int wid = blockIdx.x * kWarpsPerBlock + w;
   if (wid >= a.strips * a.chunks) return;  // the whole warp leaves together
   const int strip = wid % a.strips;
   const int chunk = wid / a.strips;
@@ -98,7 +163,6 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_stream(StreamArgs a) {
   const float4 spl = ld4(a.coef, (size_t)kSPL * P + col, inside);
   const float4 spc = ld4(a.coef, (size_t)kSPC * P + col, inside);
   const float4 spr = ld4(a.coef, (size_t)kSPR * P + col, inside);
-  constexpr bool DOWN = MODE == 1 || MODE == 2 || MODE == 5;
   float4 dw = f4zero();
   if (DOWN) dw = ld4(a.coef, (size_t)kDW * P + col, inside);
   // coarse scaling of the restricted residual: x: coarse nodes col/2 and col/2 + 1;
@@ -110,6 +174,14 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_stream(StreamArgs a) {
     cwx.y = a.ccoef[(size_t)kW * a.pc + col / 2 + 1];
   }
   if (MODE == 2 || MODE == 5) cwt = ld4(a.ccoef, (size_t)kW * a.pc + col, inside);
+  const float4 cwW4 = make_float4(a.cwW, a.cwW, a.cwW, a.cwW);
+  // prolongation only touches nodes 0..N
+  const float4 pm = make_float4(col >= 0 && col <= a.N ? 1.f : 0.f, col + 1 >= 0 && col + 1 <= a.N ? 1.f : 0.f,
+                                col + 2 >= 0 && col + 2 <= a.N ? 1.f : 0.f, col + 3 >= 0 && col + 3 <= a.N ? 1.f : 0.f);
+  // x-restriction: coarse nodes col/2 and col/2 + 1 of this lane
+  const bool own0 = owner && col <= a.N;
+  const bool own1 = owner && col + 2 <= a.N;
+  const float sx0 = col / 2 == 0 ? a.cwW : cwx.x;
 
   const int n0 = chunk * a.rows;
   const int n1 = min(a.NT + 1, n0 + a.rows);
@@ -119,230 +191,243 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_stream(StreamArgs a) {
   const int first = ADJ ? min(a.NT, n1 - 1 + WARM) : max(0, n0 - WARM);
   const int last = ADJ ? (MODE == 5 ? max(0, n0 - 1) : n0) : n1 - 1;
   const int step = ADJ ? -1 : 1;
-
-  float4 prev[S + 1];
-#pragma unroll
-  for (int k = 0; k <= S; ++k) prev[k] = f4zero();
-  float4 held = f4zero();  // t-restriction: residual of the first row of a pair
-  float4 r1 = f4zero(), r2 = f4zero();  // bilinear t-restriction: residuals of the last two rows
-
-  // Loads of the next kPF rows are issued before the current row is computed, so every
-  // warp keeps several rows of HBM traffic in flight.
   const int count = ADJ ? first - last + 1 : last - first + 1;
-  float4 qb[kPF], qu[kPF], qz[kPF], qzb[kPF];
-  float qz2[kPF];
-  auto load_row = [&](int k, float4& xb, float4& xu, float4& xz, float& xz2, float4& xzb) {
-    const bool ok = k < count;
-    const int n = first + k * step;
-    const size_t ro = (size_t)n * P;
-    xb = ld4(a.bs, ro + col, ok && inside);
-    xu = ld4(a.u_in, ro + col, ok && inside && !a.zero_init);
-    xz = f4zero();
-    xz2 = 0.f;
+
+  // Row j of the chunk (row first + j * step) goes to ring slot j % kD.
+  auto fetch = [&](const int j) {
+    const bool ok = j < count;
+    const int n = first + j * step;
+    float4* slot = &ring[w][j % kD][0][0];
+    const size_t ro = (size_t)n * P + col;
+    cp_async<16>(slot + R::kB * 32 + lane, a.bs, ro, a.bs, ok && inside);
+    if (!a.zero_init) cp_async<16>(slot + R::kU * 32 + lane, a.u_in, ro, a.bs, ok && inside);
     if (MODE == 3) {
       const int ca = col / 2;
-      if (ok && col >= 0 && ca + 1 < a.pc) {
-        const float2 t = __ldg(reinterpret_cast<const float2*>(a.z + (size_t)n * a.pc + ca));
-        xz.x = t.x;
-        xz.y = t.y;
-      }
-      if (ok && lane == 31 && col >= 0 && ca + 2 < a.pc) xz2 = a.z[(size_t)n * a.pc + ca + 2];
+      const size_t zo = (size_t)n * a.pc + ca;
+      cp_async<8>(slot + R::kZ * 32 + lane, a.z, zo, a.bs, ok && col >= 0 && ca + 1 < a.pc);
+      if (lane == 31) cp_async<4>(&slot[R::kZ * 32 + lane].z, a.z, zo + 2, a.bs, ok && col >= 0 && ca + 2 < a.pc);
     } else if (MODE == 4 || MODE == 6) {
-      xz = ld4(a.z, (size_t)(n >> 1) * a.pc + col, ok && inside);
+      cp_async<16>(slot + R::kZ * 32 + lane, a.z, (size_t)(n >> 1) * a.pc + col, a.bs, ok && inside);
     }
-    xzb = f4zero();
-    if (MODE == 6) xzb = ld4(a.z, (size_t)((n >> 1) + 1) * a.pc + col, ok && inside && (n & 1));
+    if (MODE == 6)
+      cp_async<16>(slot + R::kZB * 32 + lane, a.z, (size_t)((n >> 1) + 1) * a.pc + col, a.bs, ok && inside && (n & 1));
+    if (!DOWN && a.u64 != nullptr) {
+      cp_async<16>(slot + R::k64 * 32 + lane, a.u64, ro, a.bs, ok && inside);
+      cp_async<16>(slot + (R::k64 + 1) * 32 + lane, a.u64, ro + 2, a.bs, ok && inside);
+    }
+    cp_commit();
   };
-#pragma unroll
-  for (int p = 0; p < kPF; ++p) load_row(p, qb[p], qu[p], qz[p], qz2[p], qzb[p]);
 
-  // one row: its loads come from ring slot p, which is then refilled kPF rows ahead
-  auto process = [&](const int it, float4& sb, float4& su_, float4& sz, float& sz2, float4& szb) {
-    const int n = first + it * step;
+  // One row: consume its ring slot, sweep, store, restrict.
+  auto row = [&](auto dir_tag, const int j, const Pipe<S>& in, Pipe<S>& out) {
+    constexpr bool DIR = decltype(dir_tag)::value;
+    const int n = first + j * step;
     const bool emit = n >= n0 && n < n1;
-    const bool dir_row = n == 0;
-    const bool has_prev = ADJ ? (n < a.NT) : (n > 1);
-    const size_t rowoff = (size_t)n * P;
-    const float4 b = sb;
-    float4 cur[S + 1];
-    cur[0] = su_;
-    const float4 zr = sz;
-    const float zr2 = sz2;
-    const float4 zrb = szb;
-    load_row(it + kPF, sb, su_, sz, sz2, szb);
+    const float4* slot = &ring[w][j % kD][0][0];
+    cp_wait<kD - 1>();
+    const float4 b = slot[R::kB * 32 + lane];
+    float4 x = a.zero_init ? f4zero() : slot[R::kU * 32 + lane];
     if (MODE == 3) {
       // x-prolongation: fine 2j <- z_j, fine 2j+1 <- (z_j + z_{j+1}) / 2
-      float z2 = __shfl_down_sync(kFull, zr.x, 1);
-      if (lane == 31) z2 = zr2;
-      if (col + 0 >= 0 && col + 0 <= a.N) cur[0].x += zr.x;
-      if (col + 1 >= 0 && col + 1 <= a.N) cur[0].y += 0.5f * (zr.x + zr.y);
-      if (col + 2 >= 0 && col + 2 <= a.N) cur[0].z += zr.y;
-      if (col + 3 >= 0 && col + 3 <= a.N) cur[0].w += 0.5f * (zr.y + z2);
+      const float4 zs = slot[R::kZ * 32 + lane];
+      float z2 = __shfl_down_sync(kFull, zs.x, 1);
+      if (lane == 31) z2 = zs.z;
+      x.x = fmaf(pm.x, zs.x, x.x);
+      x.y = fmaf(pm.y, 0.5f * (zs.x + zs.y), x.y);
+      x.z = fmaf(pm.z, zs.y, x.z);
+      x.w = fmaf(pm.w, 0.5f * (zs.y + z2), x.w);
     } else if (MODE == 4 || MODE == 6) {
       // causal t-prolongation: fine rows 2m and 2m+1 <- coarse row m; bilinear: fine row
       // 2m+1 <- (z_m + z_{m+1}) / 2
-      float4 zz = zr;
-      if (MODE == 6 && (n & 1))
-        zz = make_float4(0.5f * (zr.x + zrb.x), 0.5f * (zr.y + zrb.y), 0.5f * (zr.z + zrb.z), 0.5f * (zr.w + zrb.w));
-      if (col + 0 <= a.N) cur[0].x += zz.x;
-      if (col + 1 <= a.N) cur[0].y += zz.y;
-      if (col + 2 <= a.N) cur[0].z += zz.z;
-      if (col + 3 <= a.N) cur[0].w += zz.w;
+      float4 zz = slot[R::kZ * 32 + lane];
+      if (MODE == 6) {
+        const float4 zb = slot[R::kZB * 32 + lane];
+        const float4 zh = make_float4(0.5f * (zz.x + zb.x), 0.5f * (zz.y + zb.y), 0.5f * (zz.z + zb.z),
+                                      0.5f * (zz.w + zb.w));
+        zz = sel4(n & 1, zh, zz);
+      }
+      x.x = fmaf(pm.x, zz.x, x.x);
+      x.y = fmaf(pm.y, zz.y, x.y);
+      x.z = fmaf(pm.z, zz.z, x.z);
+      x.w = fmaf(pm.w, zz.w, x.w);
     }
+    out.v[0] = x;
 #pragma unroll
     for (int k = 1; k <= S; ++k) {
-      if (k == 1 && a.zero_init) cur[1] = b;  // a sweep from zero is exactly b'
-      else cur[k] = stage(a.omc, cur[k - 1], prev[k - 1], b, dir_row, has_prev, sl, su, spl, spc, spr);
+      if (k == 1 && a.zero_init) out.v[1] = b;  // a sweep from zero is exactly b'
+      else out.v[k] = stage<DIR>(a.omc, out.v[k - 1], in.v[k - 1], b, sl, su, spl, spc, spr);
     }
-    if (emit && owner) {
-      if (a.u64) {
-        double2* q = reinterpret_cast<double2*>(a.u64 + rowoff + col);
-        double2 lo = q[0], hi = q[1];
-        lo.x += to_f64(cur[S].x);
-        lo.y += to_f64(cur[S].y);
-        hi.x += to_f64(cur[S].z);
-        hi.y += to_f64(cur[S].w);
+    if (!DOWN && a.u64 != nullptr) {
+      double2 lo = *reinterpret_cast<const double2*>(slot + R::k64 * 32 + lane);
+      double2 hi = *reinterpret_cast<const double2*>(slot + (R::k64 + 1) * 32 + lane);
+      lo.x += to_f64(out.v[S].x);
+      lo.y += to_f64(out.v[S].y);
+      hi.x += to_f64(out.v[S].z);
+      hi.y += to_f64(out.v[S].w);
+      if (emit && owner) {
+        double2* q = reinterpret_cast<double2*>(a.u64 + (size_t)n * P + col);
         q[0] = lo;
         q[1] = hi;
-      } else {
-        *reinterpret_cast<float4*>(a.u_out + rowoff + col) = cur[S];
       }
+    } else if (emit && owner) {
+      *reinterpret_cast<float4*>(a.u_out + (size_t)n * P + col) = out.v[S];
     }
     if (DOWN) {
       // scaled residual y = b' - omega u + sum S_k u_k, r = (D / omega) y
-      const float4 y = stage(-a.omega, cur[S], prev[S], b, dir_row, has_prev, sl, su, spl, spc, spr);
-      float4 r;
-      if (dir_row) {
-        r = make_float4(a.Wo * y.x, a.Wo * y.y, a.Wo * y.z, a.Wo * y.w);
-      } else {
-        r = make_float4(dw.x * y.x, dw.y * y.y, dw.z * y.z, dw.w * y.w);
-      }
+      const float4 y = stage<DIR>(-a.omega, out.v[S], in.v[S], b, sl, su, spl, spc, spr);
+      const float4 r = DIR ? make_float4(a.Wo * y.x, a.Wo * y.y, a.Wo * y.z, a.Wo * y.w) : mul4(dw, y);
+      out.r = r;
+      if (MODE == 5) out.rp = in.r;
       if (MODE == 1) {
-        float rl = __shfl_up_sync(kFull, r.w, 1);
-        if (lane == 0) rl = 0.f;
-        if (emit && owner) {
-          // b_c[j] = r[2j] + (r[2j-1] + r[2j+1]) / 2, scaled by omega / D_c
-          const int j0 = col / 2;
-          const float s0 = (n == 0 || j0 == 0) ? a.cwW : cwx.x;
-          const float s1 = (n == 0) ? a.cwW : cwx.y;
-          float* out = a.bc + (size_t)n * a.pc;
-          if (col <= a.N) out[j0] = s0 * (r.x + 0.5f * (rl + r.y));
-          if (col + 2 <= a.N) out[j0 + 1] = s1 * (r.z + 0.5f * (r.y + r.w));
-        }
-      } else if (MODE == 5) {
-        // b_c[m] = (r[2m] + (r[2m-1] + r[2m+1]) / 2) / 2 (bilinear P^T with s = 1/2), emitted
-        // when the last of the three rows arrives; r1, r2: the two rows before this one
-        int m = -1;
-        float4 sum = f4zero();
-        if (!ADJ) {
-          if ((n & 1) && n - 1 >= n0 && n - 1 < n1) {
-            m = (n - 1) >> 1;
-            const float4 lo = m >= 1 ? r2 : f4zero();
-            sum = make_float4(r1.x + 0.5f * (lo.x + r.x), r1.y + 0.5f * (lo.y + r.y), r1.z + 0.5f * (lo.z + r.z),
-                              r1.w + 0.5f * (lo.w + r.w));
-          } else if (n == a.NT && !(n & 1) && emit) {
-            m = n >> 1;
-            sum = make_float4(r.x + 0.5f * r1.x, r.y + 0.5f * r1.y, r.z + 0.5f * r1.z, r.w + 0.5f * r1.w);
-          }
-        } else {
-          if ((n & 1) && n + 1 >= n0 && n + 1 < n1) {
-            m = (n + 1) >> 1;
-            const float4 hi = n + 2 <= a.NT ? r2 : f4zero();
-            sum = make_float4(r1.x + 0.5f * (hi.x + r.x), r1.y + 0.5f * (hi.y + r.y), r1.z + 0.5f * (hi.z + r.z),
-                              r1.w + 0.5f * (hi.w + r.w));
-          } else if (n == 0 && emit) {
-            m = 0;
-            sum = make_float4(r.x + 0.5f * r1.x, r.y + 0.5f * r1.y, r.z + 0.5f * r1.z, r.w + 0.5f * r1.w);
-          }
-        }
-        if (m >= 0 && owner) {
-          float4 sc = cwt;
-          if (m == 0) sc = make_float4(a.cwW, a.cwW, a.cwW, a.cwW);
-          *reinterpret_cast<float4*>(a.bc + (size_t)m * a.pc + col) =
-              make_float4(0.5f * sc.x * sum.x, 0.5f * sc.y * sum.y, 0.5f * sc.z * sum.z, 0.5f * sc.w * sum.w);
-        }
-        r2 = r1;
-        r1 = r;
+        // b_c[j] = r[2j] + (r[2j-1] + r[2j+1]) / 2, scaled by omega / D_c
+        const float rl = __shfl_up_sync(kFull, r.w, 1);
+        const float s0 = DIR ? a.cwW : sx0;
+        const float s1 = DIR ? a.cwW : cwx.y;
+        const float2 o = make_float2(s0 * (r.x + 0.5f * (rl + r.y)), s1 * (r.z + 0.5f * (r.y + r.w)));
+        float* dst = a.bc + (size_t)n * a.pc + col / 2;
+        if (emit && own1) *reinterpret_cast<float2*>(dst) = o;
+        else if (emit && own0) dst[0] = o.x;
       } else {
-        // b_c[m] = (r[2m] + r[2m+1]) / 2 (causal P^T with s = 1/2), scaled by omega / D_c
-        const bool second = ADJ ? (n % 2 == 0) : (n % 2 == 1 || n == a.NT);
-        if (second) {
-          float4 sum = r;
-          if (ADJ ? (n + 1 <= a.NT) : (n % 2 == 1)) {
-            sum.x += held.x;
-            sum.y += held.y;
-            sum.z += held.z;
-            sum.w += held.w;
+        float4 sum;
+        int m;
+        bool put;
+        const bool odd = n & 1;
+        if (MODE == 2) {
+          // b_c[m] = (r[2m] + r[2m+1]) / 2 (causal P^T with s = 1/2); forward: emitted at
+          // row 2m+1 (row NT alone when NT is even); J^T: emitted at row 2m
+          if (!ADJ) {
+            sum = odd ? make_float4(r.x + in.r.x, r.y + in.r.y, r.z + in.r.z, r.w + in.r.w) : r;
+            put = emit && (odd || n == a.NT);
+          } else {
+            sum = make_float4(r.x + in.r.x, r.y + in.r.y, r.z + in.r.z, r.w + in.r.w);
+            put = emit && !odd;
           }
-          if (emit && owner) {
-            const int m = n >> 1;
-            float4 sc = cwt;
-            if (m == 0) sc = make_float4(a.cwW, a.cwW, a.cwW, a.cwW);
-            float4 o = make_float4(0.5f * sc.x * sum.x, 0.5f * sc.y * sum.y, 0.5f * sc.z * sum.z,
-                                   0.5f * sc.w * sum.w);
-            *reinterpret_cast<float4*>(a.bc + (size_t)m * a.pc + col) = o;
-          }
-          held = f4zero();
+          m = n >> 1;
         } else {
-          held = r;
+          // b_c[m] = (r[2m] + (r[2m-1] + r[2m+1]) / 2) / 2 (bilinear P^T with s = 1/2),
+          // emitted when the last of its three fine rows has been processed
+          const float4 so = make_float4(in.r.x + 0.5f * (in.rp.x + r.x), in.r.y + 0.5f * (in.rp.y + r.y),
+                                        in.r.z + 0.5f * (in.rp.z + r.z), in.r.w + 0.5f * (in.rp.w + r.w));
+          const float4 se = make_float4(r.x + 0.5f * in.r.x, r.y + 0.5f * in.r.y, r.z + 0.5f * in.r.z,
+                                        r.w + 0.5f * in.r.w);
+          sum = sel4(odd, so, se);
+          if (!ADJ) {
+            const int nm = n - 1;
+            m = odd ? nm >> 1 : n >> 1;
+            put = odd ? (nm >= n0 && nm < n1) : (emit && n == a.NT);
+          } else {
+            const int np = n + 1;
+            m = odd ? np >> 1 : 0;
+            put = odd ? (np >= n0 && np < n1) : (emit && n == 0);
+          }
         }
+        const float4 sc = sel4(m == 0, cwW4, cwt);
+        const float4 o = make_float4(0.5f * sc.x * sum.x, 0.5f * sc.y * sum.y, 0.5f * sc.z * sum.z, 0.5f * sc.w * sum.w);
+        if (put && owner) *reinterpret_cast<float4*>(a.bc + (size_t)m * a.pc + col) = o;
       }
     }
-#pragma unroll
-    for (int k = 0; k <= S; ++k) prev[k] = cur[k];
   };
-  for (int it = 0; it < count; it += kPF) {
+
+  Pipe<S> A, B;
 #pragma unroll
-    for (int p = 0; p < kPF; ++p)
-      if (it + p < count) process(it + p, qb[p], qu[p], qz[p], qz2[p], qzb[p]);
+  for (int k = 0; k <= S; ++k) A.v[k] = f4zero();
+  A.r = f4zero();
+  A.rp = f4zero();
+#pragma unroll
+  for (int j = 0; j < kD; ++j) fetch(j);
+  int j = 0;
+  if (!ADJ && first == 0) {
+    // row 0 is a Dirichlet row; row 1 has no coupling to it (its columns are eliminated),
+    // so the stage state handed on stays zero and only the residuals carry over
+    row(std::true_type{}, 0, A, B);
+    fetch(kD);
+    A.r = B.r;
+    A.rp = B.rp;
+    j = 1;
   }
+  const int jend = (ADJ && last == 0) ? count - 1 : count;
+  for (; j + 2 <= jend; j += 2) {
+    row(std::false_type{}, j, A, B);
+    fetch(j + kD);
+    row(std::false_type{}, j + 1, B, A);
+    fetch(j + 1 + kD);
+  }
+  if (j < jend) {
+    row(std::false_type{}, j, A, B);
+    fetch(j + kD);
+    A = B;
+    ++j;
+  }
+  if (ADJ && last == 0) row(std::true_type{}, j, A, B);
+  cp_wait<0>();
+}
+
+template <bool ADJ, int S, int MODE>
+cudaError_t launch_k(const StreamArgs& a0, cudaStream_t s) {
+  // resident blocks per SM of this instantiation (the same on every device of a process)
+  static std::atomic<int> resident{0};
+  int nb = resident.load(std::memory_order_relaxed);
+  if (nb == 0) {
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stream<ADJ, S, MODE>, kThreads, 0);
+    if (e != cudaSuccess) return e;
+    nb = nb < 1 ? 1 : nb;
+    resident.store(nb, std::memory_order_relaxed);
+  }
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  StreamArgs a = a0;
+  stream_layout(a.N, a.NT, (long long)nb * kWarpsPerBlock * sms, a);
+  const long long warps = (long long)a.strips * a.chunks;
+  const unsigned grid = (unsigned)((warps + kWarpsPerBlock - 1) / kWarpsPerBlock);
+  k_stream<ADJ, S, MODE><<<grid, kThreads, 0, s>>>(a);
+  return cudaGetLastError();
 }
 
 template <bool ADJ, int MODE>
-cudaError_t launch_mode(const StreamArgs& a, int S, unsigned grid, cudaStream_t s) {
+cudaError_t launch_mode(const StreamArgs& a, int S, cudaStream_t s) {
   switch (S) {
-    case 1: k_stream<ADJ, 1, MODE><<<grid, 32 * kWarpsPerBlock, 0, s>>>(a); break;
-    case 2: k_stream<ADJ, 2, MODE><<<grid, 32 * kWarpsPerBlock, 0, s>>>(a); break;
-    case 3: k_stream<ADJ, 3, MODE><<<grid, 32 * kWarpsPerBlock, 0, s>>>(a); break;
-    case 4: k_stream<ADJ, 4, MODE><<<grid, 32 * kWarpsPerBlock, 0, s>>>(a); break;
-    case 5: k_stream<ADJ, 5, MODE><<<grid, 32 * kWarpsPerBlock, 0, s>>>(a); break;
+    case 1: return launch_k<ADJ, 1, MODE>(a, s);
+    case 2: return launch_k<ADJ, 2, MODE>(a, s);
+    case 3: return launch_k<ADJ, 3, MODE>(a, s);
+    case 4: return launch_k<ADJ, 4, MODE>(a, s);
+    case 5: return launch_k<ADJ, 5, MODE>(a, s);
     default: return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
 }
 
 }  // namespace
 
-void stream_layout(int N, int NT, StreamArgs& a) {
+void stream_layout(int N, int NT, long long resident_warps, StreamArgs& a) {
   a.strips = (N + 1 + kOwn - 1) / kOwn;
-  // about 24 warps per SM on 152 SMs, chunks of an even number of rows in [16, 256]
-  const long long target = 152LL * 24;
+  // one wave: about one chunk per resident warp, chunks of an even number of rows in
+  // [16, 1024] (short chunks re-compute their S + 1 warm-up rows too often)
+  const long long target = resident_warps < 1 ? 1 : resident_warps;
   long long rows = ((long long)(NT + 1) * a.strips + target - 1) / target;
-  rows = rows < 16 ? 16 : (rows > 256 ? 256 : rows);
+  rows = rows < 16 ? 16 : (rows > 1024 ? 1024 : rows);
   rows += rows & 1;
   a.rows = (int)rows;
   a.chunks = (NT + 1 + a.rows - 1) / a.rows;
 }
 
 cudaError_t launch_stream(int mode, bool adj, int S, const StreamArgs& a, cudaStream_t s) {
-  const long long warps = (long long)a.strips * a.chunks;
-  const unsigned grid = (unsigned)((warps + kWarpsPerBlock - 1) / kWarpsPerBlock);
   cudaError_t e = cudaErrorInvalidValue;
   switch (mode * 2 + (adj ? 1 : 0)) {
-    case 0: e = launch_mode<false, 0>(a, S, grid, s); break;
-    case 1: e = launch_mode<true, 0>(a, S, grid, s); break;
-    case 2: e = launch_mode<false, 1>(a, S, grid, s); break;
-    case 3: e = launch_mode<true, 1>(a, S, grid, s); break;
-    case 4: e = launch_mode<false, 2>(a, S, grid, s); break;
-    case 5: e = launch_mode<true, 2>(a, S, grid, s); break;
-    case 6: e = launch_mode<false, 3>(a, S, grid, s); break;
-    case 7: e = launch_mode<true, 3>(a, S, grid, s); break;
-    case 8: e = launch_mode<false, 4>(a, S, grid, s); break;
-    case 9: e = launch_mode<true, 4>(a, S, grid, s); break;
-    case 10: e = launch_mode<false, 5>(a, S, grid, s); break;
-    case 11: e = launch_mode<true, 5>(a, S, grid, s); break;
-    case 12: e = launch_mode<false, 6>(a, S, grid, s); break;
-    case 13: e = launch_mode<true, 6>(a, S, grid, s); break;
+    case 0: e = launch_mode<false, 0>(a, S, s); break;
+    case 1: e = launch_mode<true, 0>(a, S, s); break;
+    case 2: e = launch_mode<false, 1>(a, S, s); break;
+    case 3: e = launch_mode<true, 1>(a, S, s); break;
+    case 4: e = launch_mode<false, 2>(a, S, s); break;
+    case 5: e = launch_mode<true, 2>(a, S, s); break;
+    case 6: e = launch_mode<false, 3>(a, S, s); break;
+    case 7: e = launch_mode<true, 3>(a, S, s); break;
+    case 8: e = launch_mode<false, 4>(a, S, s); break;
+    case 9: e = launch_mode<true, 4>(a, S, s); break;
+    case 10: e = launch_mode<false, 5>(a, S, s); break;
+    case 11: e = launch_mode<true, 5>(a, S, s); break;
+    case 12: e = launch_mode<false, 6>(a, S, s); break;
+    case 13: e = launch_mode<true, 6>(a, S, s); break;
     default: break;
   }
   count_launches(1);

@@ -30,12 +30,13 @@ struct StreamArgs {
   float cwW;               // coarse omega / W_Diri (DOWN)
   float* bc;               // coarse scaled right-hand side (DOWN)
   const float* z;          // coarse correction (UP)
-  // work decomposition (stream_layout)
+  // work decomposition (filled by launch_stream)
   int rows, strips, chunks;
 };
 
-// Fills rows / strips / chunks for a level of N elements and NT steps.
-void stream_layout(int N, int NT, StreamArgs& a);
+// Fills rows / strips / chunks for a level of N elements and NT steps so that one wave of
+// resident_warps warps covers it.
+void stream_layout(int N, int NT, long long resident_warps, StreamArgs& a);
 // S sweeps (1..5) in one pass of the given mode; adj selects J^T.
 cudaError_t launch_stream(int mode, bool adj, int S, const StreamArgs& a, cudaStream_t s);
 

@@ -322,18 +322,20 @@ def test_sensitivity_with_penalised_heat_capacity():
 
 
 @pytest.mark.parametrize("adj", [False, True])
-def test_mixed_precision_reaches_fp64_residual(adj):
+@pytest.mark.parametrize("inner", [1, 2])
+def test_mixed_precision_reaches_fp64_residual(adj, inner):
     w = wl.config2(N=512, NT=2048)
     N, NT, L, tT = w["N"], w["NT"], w["L"], w["tT"]
     ko, co = oracle.simp(w["chi"], w["simp"])
     bo = oracle.assemble_load(N, NT, L / N, w["q"])
-    g = pkg.Solver(N, NT, L, tT, ko, co, precision="mixed", tol=1e-8)
+    g = pkg.Solver(N, NT, L, tT, ko, co, precision="mixed", tol=1e-8, mixed_inner_cycles=inner)
     u = torch.empty((NT + 1, N + 1), dtype=torch.float64, device=DEV)
     if adj:
         st, cyc, rr = g.solve_adjoint(u, T(bo))
     else:
         st, cyc, rr = g.solve(u, b=T(bo))
     assert st == "ok" and rr < 1e-8, (st, cyc, rr)
+    assert (cyc - 3) % inner == 0  # 3 first cycles, then whole groups of inner cycles
     ue = oracle.exact(N, NT, L, tT, ko, co, bo, adj=adj)
     # true FP64 residual of the returned iterate, evaluated by the oracle
     H = oracle.Hierarchy(N, NT, L, tT, ko, co, num_levels=1)
