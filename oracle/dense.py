@@ -113,23 +113,31 @@ def coarse_material(k, c, kind, reassembly):
 
 
 class DenseHierarchy:
-    """Dense levels for a given coarsening path (string of 'x'/'t')."""
+    """Dense levels for a given coarsening path (string of 'x'/'t').
+
+    reassembly "K" / "R": every level is the all-at-once J of its own grid and averaged
+    material (Sec. 3.1, 5.1); "P": every coarse J is the Galerkin product R J P of the
+    level above (Sec. 5.1)."""
 
     def __init__(self, N, NT, L, tT, k, c, path, interp="C", reassembly="R"):
         self.levels = []
         k, c = np.asarray(k, float), np.asarray(c, float)
+        J = all_at_once(N, NT, L, tT, k, c)
         for l in range(len(path) + 1):
-            J = all_at_once(N, NT, L, tT, k, c)
             lv = dict(N=N, NT=NT, J=J, D=np.diag(J).copy(), k=k, c=c)
             if l < len(path):
                 kind = path[l]
                 P, s = prolongation(N, NT, kind, interp)
                 lv["P"], lv["R"] = P, s * P.T
-                k, c = coarse_material(k, c, kind, reassembly)
+                k, c = coarse_material(k, c, kind, "K" if reassembly == "P" else reassembly)
                 if kind == "x":
                     N //= 2
                 else:
                     NT //= 2
+                if reassembly == "P":
+                    J = lv["R"] @ lv["J"] @ P
+                else:
+                    J = all_at_once(N, NT, L, tT, k, c)
             self.levels.append(lv)
 
     def vcycle(self, l, u, b, nu=5, omega=0.5, adj=False):

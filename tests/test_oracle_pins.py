@@ -460,3 +460,85 @@ def test_optimisation_loop_descends_on_problem7():
         assert np.all((x >= 0) & (x <= 1)) and x.mean() <= 0.5 + 1e-14
     assert all(b < a for a, b in zip(thetas, thetas[1:]))
     assert thetas[-1] < 0.93 * thetas[0]
+
+
+# ---------------------------------------------------------------------------------------
+# Galerkin reassembly (P-method, Sec. 5.1): J_{l+1} = R_l J_l P_l
+# ---------------------------------------------------------------------------------------
+@pytest.mark.parametrize("interp", ["C", "B"])
+@pytest.mark.parametrize("lam", [0.02, 3.0])
+def test_galerkin_sparse_levels_match_dense_products(interp, lam):
+    from oracle.galerkin import GalerkinHierarchy
+
+    N, NT = 8, 8
+    rng = np.random.default_rng(90)
+    k, c = 10.0 ** rng.uniform(-2, 0, N), 0.5 + rng.random(N)
+    tT = lam * NT / N ** 2 / np.sqrt((k / c).min() * (k / c).max())
+    G = GalerkinHierarchy(N, NT, 1.0, tT, k, c, interp=interp, num_levels=4)
+    D = dense.DenseHierarchy(N, NT, 1.0, tT, k, c, G.path, interp=interp, reassembly="P")
+    for l in range(G.nlevels):
+        np.testing.assert_allclose(G.levels[l]["J"].toarray(), D.levels[l]["J"], rtol=0, atol=1e-12 * np.abs(D.levels[l]["J"]).max())
+    b = rng.standard_normal(G.shape(0))
+    for adj in (False, True):
+        want = D.vcycle(0, np.zeros(b.size), b.ravel(), adj=adj)
+        got = G.vcycle(np.zeros(G.shape(0)), b, adj=adj)
+        np.testing.assert_allclose(got.ravel(), want, rtol=0, atol=1e-11 * np.abs(want).max())
+
+
+@pytest.mark.parametrize("interp", ["C", "B"])
+def test_galerkin_t_coarsening_blocks_by_hand(interp):
+    """k = c = 1, N = 3, NT = 4, one t-coarsening.  With A' and B' the same-step and
+    previous-step blocks of a time row (node 0 masked to the Dirichlet row W e_0), the fine
+    rows are W I (n = 0), A' (n = 1), B' | A' (n >= 2).  Causal P = [1; 1] per pair and
+    R = P^T / 2 give coarse rows (W I + A')/2; B'/2 | A' + B'/2; B'/2 | A'/2.  Bilinear P
+    (1/2, 1, 1/2) and R = P^T / 2 give for coarse row 1: A'/8 + B'/4 | 3A'/4 + B'/2 | A'/8."""
+    from oracle.galerkin import GalerkinHierarchy
+
+    N, NT, tT = 3, 4, 0.01
+    k, c = np.ones(N), np.ones(N)
+    dx, dt = 1.0 / N, tT / NT
+    M, K = dense.global_mk(N, dx, k, c)
+    W = dense.w_diri(dx, dt, k, c)
+    E = np.diag([0.0, 1.0, 1.0, 1.0])
+    I = np.eye(N + 1)
+    A = E @ (M / dt + K) @ E + W * (I - E)
+    B = E @ (-M / dt) @ E
+    G = GalerkinHierarchy(N, NT, 1.0, tT, k, c, interp=interp, num_levels=2)
+    assert G.path == "t"
+    Jc = G.levels[1]["J"].toarray()
+    blk = lambda m, mp: Jc[m * 4:(m + 1) * 4, mp * 4:(mp + 1) * 4]  # noqa: E731
+    Z = np.zeros((4, 4))
+    if interp == "C":
+        want = {(0, 0): (W * I + A) / 2, (0, 1): Z, (1, 0): B / 2, (1, 1): A + B / 2, (1, 2): Z,
+                (2, 1): B / 2, (2, 2): A / 2}
+    else:
+        want = {(1, 0): A / 8 + B / 4, (1, 1): 3 * A / 4 + B / 2, (1, 2): A / 8}
+    for (m, mp), w in want.items():
+        np.testing.assert_allclose(blk(m, mp), w, rtol=0, atol=1e-12 * W)
+
+
+def test_galerkin_on_problem7_matches_the_paper():
+    """Sec. 5.2, problem 7 (N = NT = 256): with bilinear interpolation the Galerkin
+    hierarchy (BP) is stable up to 4 levels and blows up beyond; with causal interpolation
+    (CP) the convergence factor stays within a few percent of the K-method's (CK)."""
+    from oracle.galerkin import GalerkinHierarchy
+
+    N = NT = 256
+    p = wl.paper_problem(7, N=N, NT=NT)
+    k, c = oracle.simp(p["chi"], p["simp"])
+    b = oracle.assemble_load(N, NT, p["L"] / N, wl.load_paper(N, NT, p["L"], p["tT"]))
+
+    def rho(H, nl):
+        u, st, cyc, hist = H.solve(b, tol=1e-9, max_cycles=100)
+        return st, (hist[-1] / hist[0]) ** (1.0 / max(cyc, 1))
+
+    for nl in (4, 5, 6):
+        st, r = rho(GalerkinHierarchy(N, NT, p["L"], p["tT"], k, c, interp="B", num_levels=nl), nl)
+        if nl == 4:
+            assert st == "converged" and r < 0.6
+        else:
+            assert st == "diverged" and r > 100.0
+    for nl in (3, 5):
+        st, r = rho(GalerkinHierarchy(N, NT, p["L"], p["tT"], k, c, interp="C", num_levels=nl), nl)
+        stk, rk = rho(oracle.Hierarchy(N, NT, p["L"], p["tT"], k, c, reassembly="K", num_levels=nl), nl)
+        assert st == stk == "converged" and abs(r - rk) < 0.05 * rk
