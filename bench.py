@@ -45,7 +45,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-variant", action="store_true", help="skip the other-precision solve of the same workload")
-    p.add_argument("--mixed-inner", type=int, default=1, help="FP32 V-cycles per FP64 defect in the mixed scheme")
+    p.add_argument("--mixed-inner", type=int, default=3, help="FP32 V-cycles per FP64 defect in the mixed scheme")
     p.add_argument("--serving-requests", type=int, default=64,
                    help="requests of the 512-request serving trace to replay (0: skip serving)")
     p.add_argument("--serving-workers", type=int, default=6)
@@ -234,7 +234,7 @@ def precision_opts(args, precision):
 SERVING_OPTS = dict(precision="mixed", tol=TOL, nu=20, max_cycles=300)
 
 
-def run_serving(nreq, workers):
+def run_serving(nreq, workers, inner=3, compare=8):
     """Closed loop (all requests queued at once) for throughput, then the same requests
     with their Poisson gaps rescaled to 0.8x that throughput for latency."""
     from paper_2505_10168_gb300 import serving as sv
@@ -242,16 +242,28 @@ def run_serving(nreq, workers):
 
     reqs = wl.serving_requests()[:nreq]
     fields = lambda r: wl.request_fields(r)[:2]  # noqa: E731
+    opts = dict(SERVING_OPTS, mixed_inner_cycles=inner)
     with sv.Server(workers=workers) as srv:
-        sv.replay(srv, reqs[: min(4, nreq)], fields, speed=1e9, **SERVING_OPTS)  # warm-up
-        _, closed = sv.replay(srv, reqs, fields, speed=1e9, **SERVING_OPTS)
+        sv.replay(srv, reqs[: min(4, nreq)], fields, speed=1e9, **opts)  # warm-up
+        _, closed = sv.replay(srv, reqs, fields, speed=1e9, **opts)
         rate = closed["requests"] / closed["makespan_s"]  # requests per second
         mean_gap = (reqs[-1]["arrival"] - reqs[0]["arrival"]) / max(1, len(reqs) - 1)
         speed = 0.8 * rate * mean_gap
-        _, poisson = sv.replay(srv, reqs, fields, speed=speed, **SERVING_OPTS)
-    return {"requests": nreq, "of": 512, "workers": workers, "solver": SERVING_OPTS,
+        _, poisson = sv.replay(srv, reqs, fields, speed=speed, **opts)
+        # the same first requests, mixed and batched, against the plain FP64 single-solve
+        # form: FP64 V-cycles, one request at a time (one worker), same tolerance and cap
+        sub = reqs[: min(compare, nreq)]
+        _, batched = sv.replay(srv, sub, fields, speed=1e9, **opts)
+    fp64_opts = dict(opts, precision="fp64")
+    fp64_opts.pop("mixed_inner_cycles")
+    with sv.Server(workers=1) as one:
+        _, single = sv.replay(one, sub, fields, speed=1e9, **fp64_opts)
+    vs = {"requests": len(sub), "mixed_batched": batched, "fp64_single": single,
+          "speedup": batched["dofs_per_s"] / single["dofs_per_s"] if single["dofs_per_s"] > 0 else None}
+    return {"requests": nreq, "of": 512, "workers": workers, "solver": opts,
             "closed_loop": closed, "poisson_0.8": poisson,
-            "p50_s": poisson["p50_s"], "p99_s": poisson["p99_s"], "dofs_per_s": closed["dofs_per_s"]}
+            "p50_s": poisson["p50_s"], "p99_s": poisson["p99_s"], "dofs_per_s": closed["dofs_per_s"],
+            "vs_fp64_single": vs}
 
 
 # ----------------------------------------------------------------------------- GPU arm
@@ -420,7 +432,7 @@ def main():
         del u, q
         solver.close()
         torch.cuda.empty_cache()
-        serving = run_serving(args.serving_requests, args.serving_workers)
+        serving = run_serving(args.serving_requests, args.serving_workers, args.mixed_inner)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

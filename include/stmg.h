@@ -56,7 +56,9 @@ typedef enum {
 } stmg_status;
 
 enum { STMG_INTERP_CAUSAL = 0, STMG_INTERP_BILINEAR = 1 };  /* Sec. 3.1 / 5.1 "C" and "B" */
-enum { STMG_REASM_K = 0, STMG_REASM_R = 1, STMG_REASM_D = 2 }; /* Sec. 3.1 "K", Sec. 5.1 "R" and "D" */
+enum { STMG_REASM_K = 0, STMG_REASM_R = 1, STMG_REASM_D = 2, /* Sec. 3.1 "K", Sec. 5.1 "R" and "D" */
+       STMG_REASM_P = 3 };  /* Sec. 5.1 "P": Galerkin products J_{l+1} = R_l J_l P_l (FP64 only; the
+                               coarse k, c that Alg. 3 reads are the K averages, as in Sec. 5.1) */
 enum { STMG_FP64 = 0, STMG_MIXED = 1 };                     /* precision of the V-cycle */
 enum { STMG_COARSEST = 0, STMG_XCOARSEN = 1, STMG_TCOARSEN = 2 };
 
@@ -67,8 +69,8 @@ typedef struct {
     double lambda_crit;        /* [0.25] t-coarsen iff lambda_eff < lambda_crit (Alg. 3; Sec. 5.2 value) */
     int interp;                /* [STMG_INTERP_CAUSAL] prolongation in time: causal (copies forward)
                                   or bilinear 1/2 [1 2 1] (Sec. 5.1); x always 1/2 [1 2 1] */
-    int reassembly;            /* [STMG_REASM_R] coarse-level material averaging (STMG_REASM_D only
-                                  through stmg_create_design) */
+    int reassembly;            /* [STMG_REASM_R] coarse operators: material averaging K / R / D (D only
+                                  through stmg_create_design) or Galerkin products P */
     int min_nel;               /* [0] M of Alg. 4 (t-coarsen when N/2 < M); 0 = Alg. 3 */
     int num_levels;            /* [0] > 0: exactly this many levels N_l */
     int max_levels;            /* [30] cap on N_l when num_levels == 0 */
@@ -82,7 +84,8 @@ typedef struct {
     int max_cycles;            /* [100] cycle limit (Sec. 3.1) */
     int mixed_first_cycles;    /* [3] STMG_MIXED: FP32 V-cycles run on the first defect (an inner
                                   iteration) before the first FP64 correction; each counts as a cycle */
-    int mixed_inner_cycles;    /* [1] STMG_MIXED: FP32 V-cycles run on every later defect (1..8); the
+    int mixed_inner_cycles;    /* [3] STMG_MIXED: FP32 V-cycles run on every later defect (1..8), the
+                                  first from zero and the others continuing the FP32 iterate; the
                                   termination test is then taken every mixed_inner_cycles cycles */
 } stmg_opts;
 

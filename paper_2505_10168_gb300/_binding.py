@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(_HERE, "libstmg.so")
 
 STATUS = {0: "ok", 1: "einval", 2: "enomem", 3: "ecuda", 4: "diverged", 5: "max_cycles"}
 FP64, MIXED = 0, 1
-REASM = {"K": 0, "R": 1, "D": 2}
+REASM = {"K": 0, "R": 1, "D": 2, "P": 3}
 
 
 class STMGError(RuntimeError):

@@ -38,6 +38,14 @@ struct Level {
   double* th = nullptr;      // Thomas factors: 8 arrays of N+2 doubles
   double *u = nullptr, *b = nullptr, *t = nullptr;    // FP64 vectors
   float *u32 = nullptr, *b32 = nullptr, *t32 = nullptr;  // FP32 vectors (mixed precision)
+  // P-reassembly (levels >= 1): J as a Galerkin product in row-class form, right-hand side
+  // stored unscaled; on the coarsest level the block LU of J and of J^T
+  bool gal = false;
+  GalOp gop;
+  int* dcls = nullptr;
+  double* dgco = nullptr;
+  double* dgwd = nullptr;
+  double* dglu[2] = {nullptr, nullptr};
 };
 
 }  // namespace
@@ -148,6 +156,7 @@ void dfree(stmg_t h, T*& p) {
 void free_level(stmg_t h, Level& L) {
   dfree(h, L.dk); dfree(h, L.dc); dfree(h, L.cf64); dfree(h, L.cf32); dfree(h, L.th);
   dfree(h, L.u); dfree(h, L.b); dfree(h, L.t); dfree(h, L.u32); dfree(h, L.b32); dfree(h, L.t32);
+  dfree(h, L.dcls); dfree(h, L.dgco); dfree(h, L.dgwd); dfree(h, L.dglu[0]); dfree(h, L.dglu[1]);
 }
 
 bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
@@ -334,8 +343,46 @@ template <typename T>
 LevelView<T> view(const Level& L, double omega);
 template <>
 LevelView<double> view<double>(const Level& L, double omega) {
+  // Galerkin levels store b unscaled: their scalings are the identity (the coefficient
+  // slots kW and kDW hold 1 as well)
   return LevelView<double>{L.N, L.NT, L.pitch, make_fastdiv(L.N + 1), L.cf64, L.W, omega, 1.0 - omega,
-                           omega / L.W, L.W / omega};
+                           L.gal ? 1.0 : omega / L.W, L.gal ? 1.0 : L.W / omega};
+}
+
+GalView gal_view(const Level& L) {
+  return GalView{L.N, L.NT, L.pitch, make_fastdiv(L.N + 1), L.dcls, L.dgco, L.dgwd};
+}
+
+// Galerkin-level operations exist in FP64 only (the P-reassembly is an FP64 option).
+template <typename T>
+cudaError_t gal_sweep(const Level&, bool, const T*, const T*, T*, cudaStream_t) {
+  return cudaErrorNotSupported;
+}
+template <>
+cudaError_t gal_sweep<double>(const Level& L, bool adj, const double* u, const double* b, double* out,
+                              cudaStream_t s) {
+  return launch_gal_sweep(gal_view(L), adj, u, b, out, s);
+}
+template <typename T>
+cudaError_t gal_residual(const Level&, bool, const T*, const T*, T*, cudaStream_t) {
+  return cudaErrorNotSupported;
+}
+template <>
+cudaError_t gal_residual<double>(const Level& L, bool adj, const double* u, const double* b, double* r,
+                                 cudaStream_t s) {
+  return launch_gal_residual(gal_view(L), adj, u, b, r, s);
+}
+template <typename T>
+cudaError_t gal_exact(const Level&, bool, const T*, T*, cudaStream_t) {
+  return cudaErrorNotSupported;
+}
+template <>
+cudaError_t gal_exact<double>(const Level& L, bool adj, const double* b, double* u, cudaStream_t s) {
+  const int n = L.N + 1, M = L.NT + 1;
+  const double* G = L.dglu[adj ? 1 : 0];
+  if (!G) return cudaErrorInvalidValue;
+  const size_t nn = (size_t)M * n * n;
+  return launch_gal_exact(n, M, L.pitch, G, G + nn, G + 2 * nn, b, u, s);
 }
 template <>
 LevelView<float> view<float>(const Level& L, double omega) {
@@ -391,6 +438,7 @@ inline int transfer_type(const stmg_opts& o, const Level& L) {
 // scan for wider ones.
 template <typename T>
 cudaError_t exact_level(stmg_t h, const Level& L, bool adj, const T* bs, T* u) {
+  if (L.gal) return gal_exact<T>(L, adj, bs, u, h->s);
   if (L.N > 64) return launch_exact_par<T>(slab_view(L, h->o.omega, L.NT), adj, bs, u, h->s);
   return launch_exact<T>(thomas_view(L, h->o.omega), adj, bs, u, h->s);
 }
@@ -402,7 +450,8 @@ stmg_status smooth_level(stmg_t h, Level& L, bool adj, int nsweeps) {
   const LevelView<T> lv = view<T>(L, h->o.omega);
   for (int s = 0; s < nsweeps; ++s) {
     Vecs<T> v = vecs<T>(L);
-    CK(launch_sweep<T>(lv, adj, v.u, v.b, v.t, h->s));
+    if (L.gal) CK(gal_sweep<T>(L, adj, v.u, v.b, v.t, h->s));
+    else CK(launch_sweep<T>(lv, adj, v.u, v.b, v.t, h->s));
     set_u<T>(L, v.t);
     set_t<T>(L, v.u);
   }
@@ -424,7 +473,7 @@ stmg_status vcycle(stmg_t h, int l, bool adj, bool zero_init, bool first_done) {
   int pre = h->o.nu;
   if (zero_init && !first_done) {
     Vecs<T> v = vecs<T>(L);
-    if (pre > 0) {
+    if (pre > 0 && !L.gal) {  // (a Galerkin level keeps b unscaled: it sweeps from 0 instead)
       CK(cudaMemcpyAsync(v.u, v.b, L.nvec * sizeof(T), cudaMemcpyDeviceToDevice, h->s));
       --pre;
     } else {
@@ -437,7 +486,8 @@ stmg_status vcycle(stmg_t h, int l, bool adj, bool zero_init, bool first_done) {
   {
     Vecs<T> v = vecs<T>(L);
     Vecs<T> vc = vecs<T>(C);
-    CK(launch_residual<T>(view<T>(L, h->o.omega), adj, v.u, v.b, v.t, h->s));
+    if (L.gal) CK(gal_residual<T>(L, adj, v.u, v.b, v.t, h->s));
+    else CK(launch_residual<T>(view<T>(L, h->o.omega), adj, v.u, v.b, v.t, h->s));
     CK(launch_restrict<T>(transfer_type(h->o, L), L.N, L.NT, L.pitch, v.t, view<T>(C, h->o.omega), vc.b, h->s));
   }
   CKS(vcycle<T>(h, l + 1, adj, true, false));
@@ -769,12 +819,15 @@ stmg_status solve_loop(stmg_t h, bool adj, bool warm, int* cycles_out, double* r
 
 stmg_status check_opts(stmg_t h, const stmg_opts& o) {
   if (o.nu < 0 || !(o.omega > 0) || !std::isfinite(o.lambda_crit) || (o.interp != STMG_INTERP_CAUSAL && o.interp != STMG_INTERP_BILINEAR) ||
-      (o.reassembly != STMG_REASM_K && o.reassembly != STMG_REASM_R && o.reassembly != STMG_REASM_D) || o.min_nel < 0 || o.num_levels < 0 ||
+      (o.reassembly != STMG_REASM_K && o.reassembly != STMG_REASM_R && o.reassembly != STMG_REASM_D &&
+       o.reassembly != STMG_REASM_P) || o.min_nel < 0 || o.num_levels < 0 ||
       o.num_levels > 60 || o.max_levels < 1 || o.max_levels > 60 || o.max_coarse_dofs < 1 ||
       (o.precision != STMG_FP64 && o.precision != STMG_MIXED) || !(o.tol >= 0) || !(o.div_tol > 0) ||
       o.max_cycles < 0 || !(o.deff_fixed >= 0) || o.mixed_first_cycles < 0 || o.mixed_first_cycles > 20 ||
       o.mixed_inner_cycles < 1 || o.mixed_inner_cycles > 8)
     return fail(h, STMG_EINVAL, "invalid stmg_opts");
+  if (o.reassembly == STMG_REASM_P && o.precision != STMG_FP64)
+    return fail(h, STMG_EINVAL, "the Galerkin reassembly (STMG_REASM_P) runs in FP64 only");
   return STMG_OK;
 }
 
@@ -792,6 +845,71 @@ stmg_status read_material(stmg_t h, int n, const double* k, const double* c, std
   for (int e = 0; e < n; ++e)
     if (!finite_pos(hk[e]) || !finite_pos(hc[e]))
       return fail(h, STMG_EINVAL, "k and c must be finite and > 0 (element %d: k=%g c=%g)", e, hk[e], hc[e]);
+  return STMG_OK;
+}
+
+// P-reassembly (Sec. 5.1): every coarse operator is the Galerkin product of the level above,
+// built on the host in row-class form from level 0's per-node J entries, plus the block LU
+// of the coarsest one in both directions.  Levels >= 1 then keep their right-hand sides
+// unscaled (identity in the kW and kDW coefficient slots).
+stmg_status build_galerkin(stmg_t h) {
+  if (h->o.reassembly != STMG_REASM_P || h->lev.size() < 2) return STMG_OK;
+  Level& F = h->lev[0];
+  const size_t P0 = F.pitch;
+  std::vector<double> c0(6 * P0);
+  CK(cudaMemcpyAsync(c0.data(), F.cf64, c0.size() * sizeof(double), cudaMemcpyDeviceToHost, h->s));
+  CK(cudaStreamSynchronize(h->s));
+  GalOp op = galop_level0(F.N, F.NT, F.W, &c0[kL * P0], &c0[kD * P0], &c0[kU * P0], &c0[kPL * P0], &c0[kPC * P0],
+                          &c0[kPR * P0]);
+  for (size_t l = 1; l < h->lev.size(); ++l) {
+    Level& C = h->lev[l];
+    GalOp next;
+    if (!galop_coarsen(op, transfer_type(h->o, h->lev[l - 1]), next))
+      return fail(h, STMG_EINVAL, "Galerkin product on level %zu reaches beyond three time rows", l);
+    if (next.N != C.N || next.NT != C.NT) return fail(h, STMG_ECUDA, "internal: Galerkin level shape mismatch");
+    const size_t w = (size_t)C.N + 1;
+    std::vector<double> wd((size_t)next.ncls * w);
+    for (int c = 0; c < next.ncls; ++c)
+      for (size_t i = 0; i < w; ++i) {
+        const double d = next.co[((size_t)c * 9 + 4) * w + i];
+        if (!(d > 0.0) || !std::isfinite(d))
+          return fail(h, STMG_EINVAL, "Galerkin level %zu has a non-positive diagonal (node %zu)", l, i);
+        wd[(size_t)c * w + i] = h->o.omega / d;
+      }
+    std::vector<double> ones(C.pitch, 1.0);
+    dfree(h, C.dcls); dfree(h, C.dgco); dfree(h, C.dgwd);
+    CKS(dalloc(h, &C.dcls, next.cls.size()));
+    CKS(dalloc(h, &C.dgco, next.co.size()));
+    CKS(dalloc(h, &C.dgwd, wd.size()));
+    CK(cudaMemcpyAsync(C.dcls, next.cls.data(), next.cls.size() * sizeof(int), cudaMemcpyHostToDevice, h->s));
+    CK(cudaMemcpyAsync(C.dgco, next.co.data(), next.co.size() * sizeof(double), cudaMemcpyHostToDevice, h->s));
+    CK(cudaMemcpyAsync(C.dgwd, wd.data(), wd.size() * sizeof(double), cudaMemcpyHostToDevice, h->s));
+    CK(cudaMemcpyAsync(C.cf64 + (size_t)kW * C.pitch, ones.data(), C.pitch * sizeof(double), cudaMemcpyHostToDevice,
+                       h->s));
+    CK(cudaMemcpyAsync(C.cf64 + (size_t)kDW * C.pitch, ones.data(), C.pitch * sizeof(double),
+                       cudaMemcpyHostToDevice, h->s));
+    CK(cudaStreamSynchronize(h->s));  // the host vectors must outlive the copies
+    C.gal = true;
+    C.gop = std::move(next);
+    op = C.gop;
+  }
+  Level& Z = h->lev.back();
+  const size_t n = (size_t)Z.N + 1, M = (size_t)Z.NT + 1;
+  if (M * n * n > ((size_t)1 << 24))
+    return fail(h, STMG_EINVAL, "coarsest Galerkin level too large for its direct solver ((nt+1)(nel+1)^2 = %zu > 2^24)",
+                M * n * n);
+  for (int adj = 0; adj < 2; ++adj) {
+    std::vector<double> G, H, Ls;
+    if (!galop_block_lu(Z.gop, adj != 0, G, H, Ls))
+      return fail(h, STMG_EINVAL, "coarsest Galerkin level is singular");
+    dfree(h, Z.dglu[adj]);
+    CKS(dalloc(h, &Z.dglu[adj], G.size() + H.size() + Ls.size()));
+    CK(cudaMemcpyAsync(Z.dglu[adj], G.data(), G.size() * sizeof(double), cudaMemcpyHostToDevice, h->s));
+    CK(cudaMemcpyAsync(Z.dglu[adj] + G.size(), H.data(), H.size() * sizeof(double), cudaMemcpyHostToDevice, h->s));
+    CK(cudaMemcpyAsync(Z.dglu[adj] + G.size() + H.size(), Ls.data(), Ls.size() * sizeof(double),
+                       cudaMemcpyHostToDevice, h->s));
+    CK(cudaStreamSynchronize(h->s));
+  }
   return STMG_OK;
 }
 
@@ -813,6 +931,7 @@ stmg_status build_hierarchy(stmg_t h, const std::vector<double>& hk, const std::
   h->lev = std::move(nl);
   for (Level& L : h->lev) CKS(setup_level(h, L));
   CKS(alloc_vectors(h));
+  CKS(build_galerkin(h));
   CK(cudaStreamSynchronize(h->s));
   return STMG_OK;
 }
@@ -847,7 +966,7 @@ void stmg_default_opts(stmg_opts* o) {
   o->div_tol = 1e9;
   o->max_cycles = 100;
   o->mixed_first_cycles = 3;
-  o->mixed_inner_cycles = 1;
+  o->mixed_inner_cycles = 3;
 }
 
 const char* stmg_last_error(stmg_t h) { return h ? h->err.c_str() : g_global_error.c_str(); }
@@ -1142,7 +1261,8 @@ stmg_status stmg_apply(stmg_t h, int level, int adjoint, const double* u, double
   Level& L = h->lev[level];
   CKS(ensure_fp64(h, L));
   CKS(copy_in(h, L.u, L.pitch, u, L.NT + 1, L.N + 1));
-  CK(launch_apply<double>(view<double>(L, h->o.omega), adjoint != 0, L.u, L.t, h->s));
+  if (L.gal) CK(launch_gal_apply(gal_view(L), adjoint != 0, L.u, L.t, h->s));
+  else CK(launch_apply<double>(view<double>(L, h->o.omega), adjoint != 0, L.u, L.t, h->s));
   CKS(copy_out(h, y, L.t, L.pitch, L.NT + 1, L.N + 1));
   CK(cudaStreamSynchronize(h->s));
   return STMG_OK;
@@ -1201,6 +1321,8 @@ stmg_status stmg_exact_solve(stmg_t h, int level, int adjoint, const double* b, 
   if (!b || !u) return fail(h, STMG_EINVAL, "NULL array");
   Level& L = h->lev[level];
   if (L.N > 512 * kMaxNodesPerThread) return fail(h, STMG_EINVAL, "level too wide for the exact solver");
+  if (L.gal && level + 1 != (int)h->lev.size())
+    return fail(h, STMG_EINVAL, "Galerkin levels have a direct solver on the coarsest level only");
   CKS(ensure_fp64(h, L));
   CKS(copy_in(h, L.b, L.pitch, b, L.NT + 1, L.N + 1));
   CK(launch_scale<double>(view<double>(L, h->o.omega), true, L.b, h->s));

@@ -29,6 +29,8 @@
 
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "stmg.h"
 
 namespace stmg {
@@ -174,6 +176,43 @@ cudaError_t launch_simp(int N, const double* chi, Simp6 sp, double* k, double* c
 // constant qconst on every element) into the padded layout.
 cudaError_t launch_assemble_load(const LevelView<double>& lv, double dx, const double* q, double* bs, cudaStream_t s,
                                  double qconst = 0.0, double mult = 1.0);
+// ---- Galerkin reassembly (P-method, Sec. 5.1; stmg_galerkin.cu) ----
+// Level operator in row-class form: time row n uses coefficient set cls[n];
+// co[(c * 9 + (d + 1) * 3 + (e + 1)) * (N + 1) + i] is the coefficient of u(n + d, i + e) in
+// row (n, i).
+struct GalOp {
+  int N = 0, NT = 0, ncls = 0;
+  std::vector<int> cls;
+  std::vector<double> co;
+};
+// Level 0 (the BE-FE operator of Sec. 2.2 with the Dirichlet rows of Appendix A) from its
+// per-node J entries.
+GalOp galop_level0(int N, int NT, double W, const double* L, const double* D, const double* U, const double* PL,
+                   const double* PC, const double* PR);
+// out = R f P for a transfer of type 1 (x), 2 (causal t) or 3 (bilinear t); false if the
+// product would reach beyond three time rows.
+bool galop_coarsen(const GalOp& f, int type, GalOp& out);
+// Block-tridiagonal LU in time of J (adj: J^T): per row m, G_m = S_m^-1 and H_m = S_m^-1 U_m
+// ((N+1)^2 each, row-major) and L_m as 3 x (N+1); false if a pivot vanishes.
+bool galop_block_lu(const GalOp& op, bool adj, std::vector<double>& G, std::vector<double>& H,
+                    std::vector<double>& Lsub);
+// Device view of a row-class level: cls (NT+1), co (ncls * 9 * (N+1)), wd = omega / diagonal
+// (ncls * (N+1)).
+struct GalView {
+  int N, NT, pitch;
+  FastDiv fd;
+  const int* cls;
+  const double* co;
+  const double* wd;
+};
+cudaError_t launch_gal_apply(const GalView& g, bool adj, const double* u, double* y, cudaStream_t s);
+cudaError_t launch_gal_sweep(const GalView& g, bool adj, const double* u, const double* b, double* out,
+                             cudaStream_t s);
+cudaError_t launch_gal_residual(const GalView& g, bool adj, const double* u, const double* b, double* r,
+                                cudaStream_t s);
+cudaError_t launch_gal_exact(int n, int M, int pitch, const double* G, const double* H, const double* Lsub,
+                             const double* b, double* u, cudaStream_t s);
+
 // Projected-gradient design update of the optimisation loop (one block; out may alias chi).
 cudaError_t launch_design_update(int N, const double* chi, const double* g, double vol, double move, double* out,
                                  cudaStream_t s);

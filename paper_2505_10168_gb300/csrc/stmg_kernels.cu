@@ -292,7 +292,8 @@ __global__ void __launch_bounds__(32) k_exact(ThomasView tv, bool adj, const T* 
       const double cu = shfl_up_d(C, 1 << k);
       if (lane >= (1 << k)) C = fma(Af[k], cu, C);
     }
-    const double before = lane == 0 ? 0.0 : shfl_up_d(C, 1);
+    const double cb = shfl_up_d(C, 1);  // every lane shuffles; lane 0 then takes dp_0 = 0
+    const double before = lane == 0 ? 0.0 : cb;
     const double d0 = h0 ? a0 * before + c0 : 0.0;
     const double d1 = h1 ? C : 0.0;
     // back-substitution scan from node N down: lane value = y at node i0
@@ -302,7 +303,8 @@ __global__ void __launch_bounds__(32) k_exact(ThomasView tv, bool adj, const T* 
       const double dd = shfl_down_d(D, 1 << k);
       if (lane + (1 << k) < 32) D = fma(Eb[k], dd, D);
     }
-    const double after = lane == 31 ? 0.0 : shfl_down_d(D, 1);
+    const double da = shfl_down_d(D, 1);  // every lane shuffles; lane 31 then takes y_{N+1} = 0
+    const double after = lane == 31 ? 0.0 : da;
     const double y1 = h1 ? e1 * after + d1 : 0.0;
     const double y0 = h0 ? D : 0.0;
     T* un = u + (size_t)n * P;

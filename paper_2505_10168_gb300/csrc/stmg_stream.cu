@@ -69,22 +69,29 @@ __device__ __forceinline__ void cp_wait() {
 // One stage of the pipeline on a lane's 4 columns: out = a*x + b' + sum_k S_k x_k, with
 // a = 1 - omega for a sweep and a = -omega for the scaled residual.  DIR: a Dirichlet row
 // (time level 0), whose row of J is W_Diri I.  px is the stage input of the previous row
-// (the next row for J^T); it is zero where the stencil has no such coupling.
+// (the next row for J^T), zero where the stencil has no such coupling; pl, pr are its
+// x-neighbours across the lane boundary, which that row's own stage shuffled and handed on.
+// hl, hr receive this row's shuffled neighbours of x for the next row.
 template <bool DIR>
-__device__ __forceinline__ float4 stage(float a, const float4& x, const float4& px, const float4& b, const float4& sl,
-                                        const float4& su, const float4& spl, const float4& spc, const float4& spr) {
+__device__ __forceinline__ float4 stage(float a, const float4& x, const float4& px, float pl, float pr, float& hl,
+                                        float& hr, const float4& b, const float4& sl, const float4& su,
+                                        const float4& spl, const float4& spc, const float4& spr) {
   float4 o;
   o.x = fmaf(a, x.x, b.x);
   o.y = fmaf(a, x.y, b.y);
   o.z = fmaf(a, x.z, b.z);
   o.w = fmaf(a, x.w, b.w);
-  if (DIR) return o;
+  if (DIR) {
+    hl = 0.f;
+    hr = 0.f;
+    return o;
+  }
   // At the window edges (lanes 0 and 31) the shuffles return the lane's own values: those
   // columns are halo, whose results are never used, and every value stays finite.
   const float xl = __shfl_up_sync(kFull, x.w, 1);
   const float xr = __shfl_down_sync(kFull, x.x, 1);
-  const float pl = __shfl_up_sync(kFull, px.w, 1);
-  const float pr = __shfl_down_sync(kFull, px.x, 1);
+  hl = xl;
+  hr = xr;
   o.x = fmaf(sl.x, xl, o.x);
   o.x = fmaf(su.x, x.y, o.x);
   o.y = fmaf(sl.y, x.x, o.y);
@@ -124,15 +131,17 @@ struct Ring {
   static constexpr int kB = 0, kU = 1, kZ = 2, kZB = 3;
   static constexpr int k64 = kDown ? 0 : (MODE == 6 ? 4 : (kHasZ ? 3 : 2));
   static constexpr int kFields = kDown ? 2 : k64 + 2;
-  static constexpr int kDepth = kDown ? 6 : 4;  // rows in flight per warp
+  static constexpr int kDepth = kDown ? 8 : 4;  // rows in flight per warp (a power of two)
 };
 
 // Pipeline state after one row: v[0] the row's starting iterate (plus the prolongated
-// correction), v[k] the row after sweep k; r, rp the residuals of this row and the one
-// before it (restriction modes).
+// correction), v[k] the row after sweep k; hl[k], hr[k] the neighbours of v[k-1] across the
+// lane boundary that stage k shuffled (k = S + 1: the residual stage); r, rp the residuals
+// of this row and the one before it (restriction modes).
 template <int S>
 struct Pipe {
   float4 v[S + 1];
+  float hl[S + 2], hr[S + 2];
   float4 r, rp;
 };
 
@@ -255,7 +264,9 @@ __global__ void __launch_bounds__(kThreads, 4) k_stream(StreamArgs a) {
 #pragma unroll
     for (int k = 1; k <= S; ++k) {
       if (k == 1 && a.zero_init) out.v[1] = b;  // a sweep from zero is exactly b'
-      else out.v[k] = stage<DIR>(a.omc, out.v[k - 1], in.v[k - 1], b, sl, su, spl, spc, spr);
+      else
+        out.v[k] = stage<DIR>(a.omc, out.v[k - 1], in.v[k - 1], in.hl[k], in.hr[k], out.hl[k], out.hr[k], b, sl, su,
+                              spl, spc, spr);
     }
     if (!DOWN && a.u64 != nullptr) {
       double2 lo = *reinterpret_cast<const double2*>(slot + R::k64 * 32 + lane);
@@ -274,7 +285,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_stream(StreamArgs a) {
     }
     if (DOWN) {
       // scaled residual y = b' - omega u + sum S_k u_k, r = (D / omega) y
-      const float4 y = stage<DIR>(-a.omega, out.v[S], in.v[S], b, sl, su, spl, spc, spr);
+      const float4 y = stage<DIR>(-a.omega, out.v[S], in.v[S], in.hl[S + 1], in.hr[S + 1], out.hl[S + 1], out.hr[S + 1], b,
+                                  sl, su, spl, spc, spr);
       const float4 r = DIR ? make_float4(a.Wo * y.x, a.Wo * y.y, a.Wo * y.z, a.Wo * y.w) : mul4(dw, y);
       out.r = r;
       if (MODE == 5) out.rp = in.r;
@@ -285,8 +297,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_stream(StreamArgs a) {
         const float s1 = DIR ? a.cwW : cwx.y;
         const float2 o = make_float2(s0 * (r.x + 0.5f * (rl + r.y)), s1 * (r.z + 0.5f * (r.y + r.w)));
         float* dst = a.bc + (size_t)n * a.pc + col / 2;
-        if (emit && own1) *reinterpret_cast<float2*>(dst) = o;
-        else if (emit && own0) dst[0] = o.x;
+        if (emit && own0) dst[0] = o.x;
+        if (emit && own1) dst[1] = o.y;
       } else {
         float4 sum;
         int m;
@@ -331,6 +343,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_stream(StreamArgs a) {
   Pipe<S> A, B;
 #pragma unroll
   for (int k = 0; k <= S; ++k) A.v[k] = f4zero();
+#pragma unroll
+  for (int k = 0; k <= S + 1; ++k) A.hl[k] = A.hr[k] = 0.f;
   A.r = f4zero();
   A.rp = f4zero();
 #pragma unroll
@@ -338,7 +352,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_stream(StreamArgs a) {
   int j = 0;
   if (!ADJ && first == 0) {
     // row 0 is a Dirichlet row; row 1 has no coupling to it (its columns are eliminated),
-    // so the stage state handed on stays zero and only the residuals carry over
+    // so the stage state handed on (values and cached neighbours) stays zero and only the
+    // residuals carry over
     row(std::true_type{}, 0, A, B);
     fetch(kD);
     A.r = B.r;
@@ -402,10 +417,12 @@ cudaError_t launch_mode(const StreamArgs& a, int S, cudaStream_t s) {
 void stream_layout(int N, int NT, long long resident_warps, StreamArgs& a) {
   a.strips = (N + 1 + kOwn - 1) / kOwn;
   // one wave: about one chunk per resident warp, chunks of an even number of rows in
-  // [16, 1024] (short chunks re-compute their S + 1 warm-up rows too often)
+  // [4, 1024].  A chunk re-computes S + 1 warm-up rows, which costs little on the large
+  // levels (hundreds of rows per chunk) and nothing on the small ones, where short chunks
+  // put more of the idle warps to work and shorten the row pipeline each warp runs.
   const long long target = resident_warps < 1 ? 1 : resident_warps;
   long long rows = ((long long)(NT + 1) * a.strips + target - 1) / target;
-  rows = rows < 16 ? 16 : (rows > 1024 ? 1024 : rows);
+  rows = rows < 4 ? 4 : (rows > 1024 ? 1024 : rows);
   rows += rows & 1;
   a.rows = (int)rows;
   a.chunks = (NT + 1 + a.rows - 1) / a.rows;

@@ -2,10 +2,12 @@
 
 min Theta = b^T u dt / Theta_ref over the design chi, subject to J(chi) u = b,
 0 <= chi <= 1 and mean(chi) <= vol_frac (Sec. 7.1).  Every cycle re-assembles the levels
-for the current design on a hierarchy fixed at the start (the design-independent D_eff of
+for the current design (SIMP material, then the chosen coarse reassembly K, R, P, or D from
+the design field itself) on a hierarchy fixed at the start (the design-independent D_eff of
 Sec. 7.2 gives the same coarsening path for every design), solves the state and the
-adjoint J^T lam = b dt / Theta_ref (up to that positive factor) by STMG (warm restarts start from the previous cycle's
-u and lam; cold restarts from 0), evaluates Theta and the discrete-adjoint sensitivity,
+adjoint J^T lam = b dt / Theta_ref (up to that positive factor) by STMG (warm restarts
+start from the previous cycle's u and lam; cold restarts from 0), evaluates Theta and the
+discrete-adjoint sensitivity,
 and updates the design with ``design_update`` -- the projected-gradient step that stands
 in for the paper's MMA optimiser.  The loop stops when Theta has changed by less than rtol
 (relative) for `patience` consecutive cycles (Sec. 7.2: 0.1 % for 5 cycles).
@@ -17,7 +19,7 @@ import math
 import numpy as np
 import torch
 
-from . import Solver, design_update
+from . import Solver, design_update, simp
 
 
 def deff_simp(simp6, samples=10001):
@@ -38,10 +40,19 @@ def optimize(N, NT, L, tT, simp6, q, vol_frac=0.5, move=0.2, chi0=0.5, theta_ref
     with theta and the primal / adjoint cycle counts, statuses and relative residuals."""
     dev = torch.device(device)
     chi = torch.full((N,), float(chi0), dtype=torch.float64, device=dev)
-    opts = dict(deff_fixed=deff_simp(simp6))
+    opts = dict(deff_fixed=deff_simp(simp6), reassembly="R")
     opts.update(solver_opts)
+    design_path = opts["reassembly"] == "D"
     history = []
-    with Solver(N, NT, L, tT, chi=chi, simp6=simp6, **opts) as solver:
+    if design_path:  # D-reassembly re-applies SIMP on every level itself
+        opts.pop("reassembly")
+        solver = Solver(N, NT, L, tT, chi=chi, simp6=simp6, **opts)
+    else:  # K, R, P: the material of the current design, by the SIMP kernel
+        k = torch.empty_like(chi)
+        c = torch.empty_like(chi)
+        simp(chi, simp6, k, c)
+        solver = Solver(N, NT, L, tT, k, c, **opts)
+    with solver:
         qd = torch.as_tensor(np.ascontiguousarray(q), dtype=torch.float64, device=dev)
         b = torch.empty((NT + 1, N + 1), dtype=torch.float64, device=dev)
         solver.assemble_load(qd, b)
@@ -54,7 +65,11 @@ def optimize(N, NT, L, tT, simp6, q, vol_frac=0.5, move=0.2, chi0=0.5, theta_ref
         calm = 0
         for it in range(max_iter):
             if it > 0:
-                solver.update_design(chi)
+                if design_path:
+                    solver.update_design(chi)
+                else:
+                    simp(chi, simp6, k, c)
+                    solver.update_material(k, c)
             restart = warm and it > 0
             st_u, cyc_u, rr_u = solver.solve(u, b=b, warm=restart)
             st_l, cyc_l, rr_l = solver.solve_adjoint(lam, b, warm=restart)
@@ -81,7 +96,7 @@ def main():
     ap = argparse.ArgumentParser(description=main.__doc__)
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--interp", default="C", choices=["C", "B"])
-    ap.add_argument("--reassembly", default="R", choices=["K", "R"])
+    ap.add_argument("--reassembly", default="R", choices=["K", "R", "D", "P"])
     ap.add_argument("--cold", action="store_true")
     ap.add_argument("--max-iter", type=int, default=200)
     a = ap.parse_args()

@@ -61,15 +61,16 @@ def test_optimisation_loop_matches_oracle():
     np.testing.assert_allclose(r["chi"], designs[iters + 1], rtol=0, atol=1e-6)
 
 
-def test_problem7_optimisation_robustness():
-    """Sec. 7.3 at N = NT = 256, N_l = 6, nu = 20, causal interpolation, R-reassembly."""
+@pytest.mark.parametrize("interp,reassembly", [("C", "R"), ("B", "R"), ("C", "P")])
+def test_problem7_optimisation_robustness(interp, reassembly):
+    """Sec. 7.3 at N = NT = 256, N_l = 6, nu = 20 with the CR, BR and CP methods."""
     N = NT = 256
     p = wl.paper_problem(7, N=N, NT=NT)
     q = wl.load_paper(N, NT, p["L"], p["tT"])
     runs = {}
     for warm in (True, False):
         r = optimize(N, NT, p["L"], p["tT"], p["simp"], q, warm=warm, max_iter=40, patience=100, num_levels=6, nu=20,
-                     tol=1e-9, max_cycles=200)
+                     tol=1e-9, max_cycles=200, interp=interp, reassembly=reassembly)
         hist = r["history"]
         assert all(h["status"] == "ok" and h["adj_status"] == "ok" for h in hist)
         assert max(max(h["cycles"], h["adj_cycles"]) for h in hist) < 80
