@@ -143,7 +143,7 @@ def oracle_sample(w, nt_sample, tol=TOL):
     tT = w["tT"] * nt_sample / w["NT"]
     q = np.ascontiguousarray(w["q"][: nt_sample + 1])
     t0 = time.perf_counter()
-    H = oracle.Hierarchy(N, nt_sample, w["L"], tT, k, c)
+    H = oracle.Hierarchy(N, nt_sample, w["L"], tT, k, c, nu=w.get("nu", 5))
     b = oracle.assemble_load(N, nt_sample, w["L"] / N, q)
     u, st, cyc, hist = H.solve(b, tol=tol)
     dt = time.perf_counter() - t0
@@ -162,20 +162,30 @@ def oracle_time_stepping(w):
         k, c = w["k"], w["c"]
     t0 = time.perf_counter()
     b = oracle.assemble_load(N, NT, w["L"] / N, w["q"])
-    oracle.exact(N, NT, w["L"], w["tT"], k, c, b)
+    u = oracle.exact(N, NT, w["L"], w["tT"], k, c, b)
     dt = time.perf_counter() - t0
-    return dict(value=(N + 1) * (NT + 1) / dt, seconds=dt)
+    return dict(value=(N + 1) * (NT + 1) / dt, seconds=dt, u=u)
 
 
-def cpu_baseline_obj(w, nt_sample=256):
+def cpu_baseline_obj(w, nt_sample=256, solutions=None):
+    """The timed oracle legs; `solutions` (name -> host solution of the full workload) are
+    compared with the oracle's exact solution, which the time-stepping leg produces."""
+    nt_sample = min(nt_sample, w["NT"])
     s = oracle_sample(w, nt_sample)
     ts = oracle_time_stepping(w)
+    acc = None
+    if solutions:
+        ue = ts["u"]
+        scale = float(np.abs(ue).max())
+        acc = {name: float(np.abs(v - ue).max() / scale) for name, v in solutions.items()}
+        acc["what"] = "max |u - u_exact| / max |u_exact| against the oracle's exact time stepping on the full grid"
     return {"value": s["value"], "unit": "DOF/s", "cores": 1, "kind": "oracle",
             "sample": "oracle STMG (FP64 C, Alg. 1 with the same options) solving the first %d of %d time steps "
                       "of the workload (%d DOFs, same dx, dt, material and load) to %.0e: %d cycles in %.1f s"
                       % (nt_sample, w["NT"], s["dofs"], TOL, s["cycles"], s["seconds"]),
             "time_stepping": {"value": ts["value"], "unit": "DOF/s", "seconds": ts["seconds"],
-                              "what": "oracle exact sequential time stepping (Thomas per step) on the full grid"}}
+                              "what": "oracle exact sequential time stepping (Thomas per step) on the full grid"},
+            "accuracy": acc}
 
 
 def run_reference(args):
@@ -183,7 +193,7 @@ def run_reference(args):
     if rank != 0:
         return
     w = load_workload(args.workload)
-    nt_sample = 128
+    nt_sample = min(128, w["NT"])
     for _ in range(args.warmup):
         oracle_sample(w, nt_sample)
     vals, secs = [], []
@@ -229,6 +239,11 @@ def whole_job_rate(units_per_rank, world, seconds):
 def precision_opts(args, precision):
     """Solver options that only the mixed scheme takes."""
     return {"mixed_inner_cycles": args.mixed_inner} if precision == "mixed" else {}
+
+
+def workload_opts(w):
+    """Solver options the workload fixes (nu = 20 for the rough differentiation field)."""
+    return {"nu": w["nu"]} if "nu" in w else {}
 
 
 SERVING_OPTS = dict(precision="mixed", tol=TOL, nu=20, max_cycles=300)
@@ -304,7 +319,8 @@ def main():
     u = torch.empty((NT + 1, N + 1), dtype=torch.float64, device=dev)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    solver = pkg.Solver(N, NT, L, tT, k, c, precision=args.precision, tol=TOL, **precision_opts(args, args.precision))
+    solver = pkg.Solver(N, NT, L, tT, k, c, precision=args.precision, tol=TOL, **precision_opts(args, args.precision),
+                        **workload_opts(w))
     setup_ms = 1e3 * (time.perf_counter() - t0)
     levels, path = solver.num_levels, solver.path()
 
@@ -334,6 +350,8 @@ def main():
     cycles = statuses[-1][1]
     relres = statuses[-1][2]
     ok = all(s[0] == "ok" and s[2] < TOL for s in statuses)
+    check = rank == 0 and world == 1 and not args.no_cpu_baseline
+    solutions = {args.precision: u.cpu().numpy()} if check else {}
 
     # ---- dominant kernel: FP64 Jacobi sweep on the finest level, timed live ----
     roofline = None
@@ -409,7 +427,7 @@ def main():
     variant = None
     if not args.no_variant:
         other = "mixed" if args.precision == "fp64" else "fp64"
-        s2 = pkg.Solver(N, NT, L, tT, k, c, precision=other, tol=TOL, **precision_opts(args, other))
+        s2 = pkg.Solver(N, NT, L, tT, k, c, precision=other, tol=TOL, **precision_opts(args, other), **workload_opts(w))
         for _ in range(max(1, args.warmup)):
             s2.solve(u, q=q)
         torch.cuda.synchronize()
@@ -419,6 +437,8 @@ def main():
         st2 = [s2.solve(u, q=q) for _ in range(args.steps)]
         e1.record(stream)
         torch.cuda.synchronize()
+        if check:
+            solutions[other] = u.cpu().numpy()
         ms2 = e0.elapsed_time(e1) / args.steps
         variant = {"precision": other, "value": world * dofs / (ms2 * 1e-3), "unit": "DOF/s", "ms_per_step": ms2,
                    "cycles": st2[-1][1], "relres": st2[-1][2],
@@ -435,8 +455,9 @@ def main():
         serving = run_serving(args.serving_requests, args.serving_workers, args.mixed_inner)
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline_obj(w)
+    if check:
+        cpu = cpu_baseline_obj(w, solutions=solutions)
+        del solutions
 
     if rank == 0:
         out = {
@@ -444,13 +465,14 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
             "data": "synthetic",
-            "config": {"workload": w["name"], "N": N, "NT": NT, "dofs": dofs, "precision": args.precision, **precision_opts(args, args.precision),
+            "config": {"workload": w["name"], "N": N, "NT": NT, "dofs": dofs, "precision": args.precision, **precision_opts(args, args.precision), **workload_opts(w),
                        "tol": TOL, "levels": levels, "path": path, "cycles": cycles,
                        "relres": relres, "converged": ok, "setup_ms": setup_ms,
                        "l2": "no flush: every vector (%d MB) exceeds the 129 MB L2" % (dofs * 8 // 2 ** 20),
                        "parallelism": "replicas" if world > 1 else "single"},
             "clocks": clocks, "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline,
             "cpu_baseline": cpu, "variant": variant, "gpu_time_stepping": gpu_ts, "serving": serving,
+            "accuracy": cpu.pop("accuracy", None) if cpu else None,
         }
         print(json.dumps(out))
     if world > 1:

@@ -45,7 +45,7 @@ enum CoefSlot {
 
 inline int level_pitch(int N) {
   int need = N + 2;
-  int align = need > 64 ? 32 : 4;
+  int align = need > 64 ? 32 : 8;
   return (need + align - 1) / align * align;
 }
 

@@ -1,6 +1,7 @@
 // stmg_stream.cu -- fused FP32 passes of the V-cycle for the mixed-precision scheme.
 //
-// One warp owns a window of 128 columns (4 per lane, float4) of one level and marches
+// One warp owns a window of 32 * kVec columns (kVec per lane: 8 in the DOWN passes, 4 in
+// the others) of one level and marches
 // through a chunk of time rows.  Because the space-time stencil couples row n only to
 // rows n and n-1 (n+1 for the adjoint), S damped-Jacobi sweeps (Sec. 3.1) are a pipeline
 // over rows: sweep k of row n needs sweep k-1 of rows n and n-1, so a warp keeps the
@@ -8,15 +9,16 @@
 // the row is read.  The same pipeline then evaluates the residual and restricts it
 // (Sec. 3.1, R = s P^T) to the coarse level (DOWN pass), or adds the prolongated coarse
 // correction before sweeping (UP pass).  x-neighbours come from warp shuffles; the window
-// carries an 8-column halo on each side and a chunk starts S(+1) rows early, so every
-// output value is computed from exact inputs with no block-level synchronisation.
+// carries an 8-column halo on each side and a chunk starts S(+1) rows early, so every output
+// value is computed from exact inputs with no block-level synchronisation.
 //
 // A row's inputs (b', the starting iterate, the coarse correction, the FP64 iterate) are
 // staged through a per-warp ring of rows in shared memory, filled by asynchronous copies
 // several rows ahead, so the loads in flight cost no registers.  The row loop has no
 // data-dependent branches: the Dirichlet row 0 is peeled off, rows alternate between two
 // register sets of pipeline state, and every row-dependent choice is a select or a
-// predicated store.
+// predicated store.  Each lane holds kVec consecutive columns, so the per-row bookkeeping
+// (ring, predicates, addresses, shuffles) is spread over that many DOFs.
 //
 // HBM traffic per DOF of a level (x-coarsening, zero start): DOWN reads b' and writes u
 // and b'_c (10 B); UP reads u, b', z and writes u (14 B); the finest-level UP of the
@@ -30,18 +32,73 @@
 namespace stmg {
 namespace {
 
-constexpr int kVec = 4;
-constexpr int kWin = 32 * kVec;            // columns per warp window
-constexpr int kHalo = 8;                   // halo columns on each side
-constexpr int kOwn = kWin - 2 * kHalo;     // 112 columns owned per window
-constexpr int kWarpsPerBlock = 4;
-constexpr int kThreads = 32 * kWarpsPerBlock;
 constexpr unsigned kFull = 0xffffffffu;
 
-__device__ __forceinline__ float4 f4zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+// Columns per lane by pass: the DOWN passes (issue-bound) hold 8, which halves their
+// per-DOF bookkeeping and halo overhead; the UP and plain passes (latency-bound, with more
+// streams and the FP64 accumulate) hold 4, which keeps twice as many warps resident.
+template <int MODE>
+struct Width {
+  static constexpr bool kDown = MODE == 1 || MODE == 2 || MODE == 5;
+  static constexpr int kVec = kDown ? 8 : 4;          // columns per lane
+  static constexpr int kWarpsPerBlock = kDown ? 2 : 4;
+  static constexpr int kThreads = 32 * kWarpsPerBlock;
+  static constexpr int kMinBlocks = kDown ? 1 : 4;    // 4-column passes: <= 128 registers
+  static constexpr int kHalo = 8;                     // halo columns on each side
+  static constexpr int kOwn = 32 * kVec - 2 * kHalo;  // columns owned per window
+  // S <= 5 sweeps and the residual spoil at most 6 columns from each window edge, and the
+  // x-restriction reads one more: the halo must cover 7 and be whole lanes.
+  static_assert(kHalo >= 7 && kHalo % kVec == 0, "halo must cover 7 columns in whole lanes");
+};
 
-__device__ __forceinline__ float4 ld4(const float* __restrict__ p, size_t off, bool ok) {
-  return ok ? __ldg(reinterpret_cast<const float4*>(p + off)) : f4zero();
+template <int V>
+struct Vf {
+  static_assert(V % 4 == 0, "lanes hold whole float4");
+  float e[V];
+};
+
+template <int V>
+__device__ __forceinline__ Vf<V> vzero() {
+  Vf<V> v;
+#pragma unroll
+  for (int j = 0; j < V; ++j) v.e[j] = 0.f;
+  return v;
+}
+
+template <int V>
+__device__ __forceinline__ Vf<V> ldv(const float* __restrict__ p, size_t off, bool ok) {
+  Vf<V> v;
+#pragma unroll
+  for (int q = 0; q < V / 4; ++q) {
+    const float4 t = ok ? __ldg(reinterpret_cast<const float4*>(p + off) + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+    v.e[4 * q] = t.x;
+    v.e[4 * q + 1] = t.y;
+    v.e[4 * q + 2] = t.z;
+    v.e[4 * q + 3] = t.w;
+  }
+  return v;
+}
+
+// V floats of lane `lane` from field `f` (V / 4 float4 wide) of a ring slot.
+template <int V>
+__device__ __forceinline__ Vf<V> lds_v(const float4* slot, int f, int lane) {
+  Vf<V> v;
+#pragma unroll
+  for (int q = 0; q < V / 4; ++q) {
+    const float4 t = slot[(f + q) * 32 + lane];
+    v.e[4 * q] = t.x;
+    v.e[4 * q + 1] = t.y;
+    v.e[4 * q + 2] = t.z;
+    v.e[4 * q + 3] = t.w;
+  }
+  return v;
+}
+
+template <int V>
+__device__ __forceinline__ void stg_v(float* p, const Vf<V>& v) {
+#pragma unroll
+  for (int q = 0; q < V / 4; ++q)
+    reinterpret_cast<float4*>(p)[q] = make_float4(v.e[4 * q], v.e[4 * q + 1], v.e[4 * q + 2], v.e[4 * q + 3]);
 }
 
 // Asynchronous global -> shared copies of base[off ...]; when ok is false nothing is read
@@ -66,21 +123,24 @@ __device__ __forceinline__ void cp_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-// One stage of the pipeline on a lane's 4 columns: out = a*x + b' + sum_k S_k x_k, with
+// The lane's columns of the five scaled neighbour coefficients -omega c_k / D.
+template <int V>
+struct Coefs {
+  Vf<V> sl, su, spl, spc, spr;
+};
+
+// One stage of the pipeline on a lane's columns: out = a*x + b' + sum_k S_k x_k, with
 // a = 1 - omega for a sweep and a = -omega for the scaled residual.  DIR: a Dirichlet row
 // (time level 0), whose row of J is W_Diri I.  px is the stage input of the previous row
 // (the next row for J^T), zero where the stencil has no such coupling; pl, pr are its
 // x-neighbours across the lane boundary, which that row's own stage shuffled and handed on.
 // hl, hr receive this row's shuffled neighbours of x for the next row.
-template <bool DIR>
-__device__ __forceinline__ float4 stage(float a, const float4& x, const float4& px, float pl, float pr, float& hl,
-                                        float& hr, const float4& b, const float4& sl, const float4& su,
-                                        const float4& spl, const float4& spc, const float4& spr) {
-  float4 o;
-  o.x = fmaf(a, x.x, b.x);
-  o.y = fmaf(a, x.y, b.y);
-  o.z = fmaf(a, x.z, b.z);
-  o.w = fmaf(a, x.w, b.w);
+template <bool DIR, int V>
+__device__ __forceinline__ Vf<V> stage(float a, const Vf<V>& x, const Vf<V>& px, float pl, float pr, float& hl,
+                                       float& hr, const Vf<V>& b, const Coefs<V>& cf) {
+  Vf<V> o;
+#pragma unroll
+  for (int j = 0; j < V; ++j) o.e[j] = fmaf(a, x.e[j], b.e[j]);
   if (DIR) {
     hl = 0.f;
     hr = 0.f;
@@ -88,72 +148,66 @@ __device__ __forceinline__ float4 stage(float a, const float4& x, const float4& 
   }
   // At the window edges (lanes 0 and 31) the shuffles return the lane's own values: those
   // columns are halo, whose results are never used, and every value stays finite.
-  const float xl = __shfl_up_sync(kFull, x.w, 1);
-  const float xr = __shfl_down_sync(kFull, x.x, 1);
+  const float xl = __shfl_up_sync(kFull, x.e[V - 1], 1);
+  const float xr = __shfl_down_sync(kFull, x.e[0], 1);
   hl = xl;
   hr = xr;
-  o.x = fmaf(sl.x, xl, o.x);
-  o.x = fmaf(su.x, x.y, o.x);
-  o.y = fmaf(sl.y, x.x, o.y);
-  o.y = fmaf(su.y, x.z, o.y);
-  o.z = fmaf(sl.z, x.y, o.z);
-  o.z = fmaf(su.z, x.w, o.z);
-  o.w = fmaf(sl.w, x.z, o.w);
-  o.w = fmaf(su.w, xr, o.w);
-  o.x = fmaf(spl.x, pl, o.x);
-  o.x = fmaf(spc.x, px.x, o.x);
-  o.x = fmaf(spr.x, px.y, o.x);
-  o.y = fmaf(spl.y, px.x, o.y);
-  o.y = fmaf(spc.y, px.y, o.y);
-  o.y = fmaf(spr.y, px.z, o.y);
-  o.z = fmaf(spl.z, px.y, o.z);
-  o.z = fmaf(spc.z, px.z, o.z);
-  o.z = fmaf(spr.z, px.w, o.z);
-  o.w = fmaf(spl.w, px.z, o.w);
-  o.w = fmaf(spc.w, px.w, o.w);
-  o.w = fmaf(spr.w, pr, o.w);
+#pragma unroll
+  for (int j = 0; j < V; ++j) {
+    const float left = j == 0 ? xl : x.e[j - 1];
+    const float right = j == V - 1 ? xr : x.e[j + 1];
+    const float pleft = j == 0 ? pl : px.e[j - 1];
+    const float pright = j == V - 1 ? pr : px.e[j + 1];
+    float t = fmaf(cf.sl.e[j], left, o.e[j]);
+    t = fmaf(cf.su.e[j], right, t);
+    t = fmaf(cf.spl.e[j], pleft, t);
+    t = fmaf(cf.spc.e[j], px.e[j], t);
+    o.e[j] = fmaf(cf.spr.e[j], pright, t);
+  }
   return o;
 }
 
-__device__ __forceinline__ float4 mul4(const float4& s, const float4& v) {
-  return make_float4(s.x * v.x, s.y * v.y, s.z * v.z, s.w * v.w);
-}
-__device__ __forceinline__ float4 sel4(bool c, const float4& p, const float4& q) {
-  return make_float4(c ? p.x : q.x, c ? p.y : q.y, c ? p.z : q.z, c ? p.w : q.w);
-}
-
-// Fields of one ring slot, 16 bytes per lane each: b', the starting iterate, the coarse
-// correction rows (UP), the FP64 iterate (two fields; UP and plain passes).
+// Fields of one ring slot, kQ float4 per lane each (the FP64 iterate: 2 kQ): b', the
+// starting iterate, the coarse correction rows (UP), the FP64 iterate (UP and plain passes).
 template <int MODE>
 struct Ring {
-  static constexpr bool kDown = MODE == 1 || MODE == 2 || MODE == 5;
+  static constexpr bool kDown = Width<MODE>::kDown;
+  static constexpr int kQ = Width<MODE>::kVec / 4;
   static constexpr bool kHasZ = MODE == 3 || MODE == 4 || MODE == 6;
-  static constexpr int kB = 0, kU = 1, kZ = 2, kZB = 3;
-  static constexpr int k64 = kDown ? 0 : (MODE == 6 ? 4 : (kHasZ ? 3 : 2));
-  static constexpr int kFields = kDown ? 2 : k64 + 2;
-  static constexpr int kDepth = kDown ? 8 : 4;  // rows in flight per warp (a power of two)
+  static constexpr int kB = 0, kU = kQ, kZ = 2 * kQ, kZB = 3 * kQ;
+  static constexpr int k64 = kDown ? 0 : (MODE == 6 ? 4 * kQ : (kHasZ ? 3 * kQ : 2 * kQ));
+  static constexpr int kWidth = kDown ? 2 * kQ : k64 + 2 * kQ;  // float4 per lane and slot
+  static constexpr int kDepth = 4;                               // rows in flight per warp
 };
 
 // Pipeline state after one row: v[0] the row's starting iterate (plus the prolongated
 // correction), v[k] the row after sweep k; hl[k], hr[k] the neighbours of v[k-1] across the
 // lane boundary that stage k shuffled (k = S + 1: the residual stage); r, rp the residuals
 // of this row and the one before it (restriction modes).
-template <int S>
+template <int S, int V>
 struct Pipe {
-  float4 v[S + 1];
+  Vf<V> v[S + 1];
   float hl[S + 2], hr[S + 2];
-  float4 r, rp;
+  Vf<V> r, rp;
 };
 
 // MODE: 0 plain sweeps, 1 sweeps + residual + x-restriction, 2 sweeps + residual +
 // causal t-restriction, 3 x-prolongation + sweeps, 4 causal t-prolongation + sweeps,
 // 5 sweeps + residual + bilinear t-restriction, 6 bilinear t-prolongation + sweeps.
 template <bool ADJ, int S, int MODE>
-__global__ void __launch_bounds__(kThreads, 4) k_stream(StreamArgs a) {
+__global__ void __launch_bounds__(Width<MODE>::kThreads, Width<MODE>::kMinBlocks) k_stream(StreamArgs a) {
   using R = Ring<MODE>;
+  using Wd = Width<MODE>;
+  constexpr int kVec = Wd::kVec;
+  constexpr int kQ = kVec / 4;
+  constexpr int kHalo = Wd::kHalo;
+  constexpr int kOwn = Wd::kOwn;
+  constexpr int kWarpsPerBlock = Wd::kWarpsPerBlock;
+  using V = Vf<kVec>;
   constexpr bool DOWN = R::kDown;
   constexpr int kD = R::kDepth;
-  __shared__ float4 ring[kWarpsPerBlock][kD][R::kFields][32];
+  constexpr int kSlot = R::kWidth * 32;  // float4 per slot
+  __shared__ float4 ring[kWarpsPerBlock * kD * kSlot];
 
   const int lane = threadIdx.x & 31;
   const int w = threadIdx.x >> 5;
@@ -162,35 +216,36 @@ __global__ void __launch_bounds__(kThreads, 4) k_stream(StreamArgs a) {
   const int strip = wid % a.strips;
   const int chunk = wid / a.strips;
   const int c0 = strip * kOwn - kHalo;
-  const int col = c0 + kVec * lane;  // multiple of 4; either fully inside [0, pitch) or fully outside
+  const int col = c0 + kVec * lane;  // multiple of kVec; either fully inside [0, pitch) or fully outside
   const bool inside = col >= 0 && col + kVec <= a.pitch;
   const bool owner = lane >= kHalo / kVec && lane < (kHalo + kOwn) / kVec && inside;
   const int P = a.pitch;
+  float4* wring = ring + (size_t)w * kD * kSlot;
 
-  const float4 sl = ld4(a.coef, (size_t)kSL * P + col, inside);
-  const float4 su = ld4(a.coef, (size_t)kSU * P + col, inside);
-  const float4 spl = ld4(a.coef, (size_t)kSPL * P + col, inside);
-  const float4 spc = ld4(a.coef, (size_t)kSPC * P + col, inside);
-  const float4 spr = ld4(a.coef, (size_t)kSPR * P + col, inside);
-  float4 dw = f4zero();
-  if (DOWN) dw = ld4(a.coef, (size_t)kDW * P + col, inside);
-  // coarse scaling of the restricted residual: x: coarse nodes col/2 and col/2 + 1;
-  // t: coarse node = fine node
-  float2 cwx = make_float2(0.f, 0.f);
-  float4 cwt = f4zero();
-  if (MODE == 1 && inside && col / 2 + 1 < a.pc) {
-    cwx.x = a.ccoef[(size_t)kW * a.pc + col / 2];
-    cwx.y = a.ccoef[(size_t)kW * a.pc + col / 2 + 1];
+  Coefs<kVec> cf;
+  cf.sl = ldv<kVec>(a.coef, (size_t)kSL * P + col, inside);
+  cf.su = ldv<kVec>(a.coef, (size_t)kSU * P + col, inside);
+  cf.spl = ldv<kVec>(a.coef, (size_t)kSPL * P + col, inside);
+  cf.spc = ldv<kVec>(a.coef, (size_t)kSPC * P + col, inside);
+  cf.spr = ldv<kVec>(a.coef, (size_t)kSPR * P + col, inside);
+  V dw = vzero<kVec>();
+  if (DOWN) dw = ldv<kVec>(a.coef, (size_t)kDW * P + col, inside);
+  // coarse scaling of the restricted residual: x: coarse nodes col/2 .. col/2 + kVec/2 - 1
+  // (node 0 is a Dirichlet node); t: coarse node = fine node (row 0: Dirichlet rows)
+  constexpr int kH = kVec / 2;
+  float cwx[kH];
+  const int ca = col / 2;
+#pragma unroll
+  for (int q = 0; q < kH; ++q) {
+    cwx[q] = 0.f;
+    if (MODE == 1 && inside && ca + q < a.pc) cwx[q] = ca + q == 0 ? a.cwW : a.ccoef[(size_t)kW * a.pc + ca + q];
   }
-  if (MODE == 2 || MODE == 5) cwt = ld4(a.ccoef, (size_t)kW * a.pc + col, inside);
-  const float4 cwW4 = make_float4(a.cwW, a.cwW, a.cwW, a.cwW);
+  V cwt = vzero<kVec>();
+  if (MODE == 2 || MODE == 5) cwt = ldv<kVec>(a.ccoef, (size_t)kW * a.pc + col, inside);
   // prolongation only touches nodes 0..N
-  const float4 pm = make_float4(col >= 0 && col <= a.N ? 1.f : 0.f, col + 1 >= 0 && col + 1 <= a.N ? 1.f : 0.f,
-                                col + 2 >= 0 && col + 2 <= a.N ? 1.f : 0.f, col + 3 >= 0 && col + 3 <= a.N ? 1.f : 0.f);
-  // x-restriction: coarse nodes col/2 and col/2 + 1 of this lane
-  const bool own0 = owner && col <= a.N;
-  const bool own1 = owner && col + 2 <= a.N;
-  const float sx0 = col / 2 == 0 ? a.cwW : cwx.x;
+  V pm;
+#pragma unroll
+  for (int j = 0; j < kVec; ++j) pm.e[j] = col + j >= 0 && col + j <= a.N ? 1.f : 0.f;
 
   const int n0 = chunk * a.rows;
   const int n1 = min(a.NT + 1, n0 + a.rows);
@@ -206,123 +261,140 @@ __global__ void __launch_bounds__(kThreads, 4) k_stream(StreamArgs a) {
   auto fetch = [&](const int j) {
     const bool ok = j < count;
     const int n = first + j * step;
-    float4* slot = &ring[w][j % kD][0][0];
+    float4* slot = wring + (j % kD) * kSlot;
     const size_t ro = (size_t)n * P + col;
-    cp_async<16>(slot + R::kB * 32 + lane, a.bs, ro, a.bs, ok && inside);
-    if (!a.zero_init) cp_async<16>(slot + R::kU * 32 + lane, a.u_in, ro, a.bs, ok && inside);
-    if (MODE == 3) {
-      const int ca = col / 2;
-      const size_t zo = (size_t)n * a.pc + ca;
-      cp_async<8>(slot + R::kZ * 32 + lane, a.z, zo, a.bs, ok && col >= 0 && ca + 1 < a.pc);
-      if (lane == 31) cp_async<4>(&slot[R::kZ * 32 + lane].z, a.z, zo + 2, a.bs, ok && col >= 0 && ca + 2 < a.pc);
-    } else if (MODE == 4 || MODE == 6) {
-      cp_async<16>(slot + R::kZ * 32 + lane, a.z, (size_t)(n >> 1) * a.pc + col, a.bs, ok && inside);
+#pragma unroll
+    for (int q = 0; q < kQ; ++q) cp_async<16>(slot + (R::kB + q) * 32 + lane, a.bs, ro + 4 * q, a.bs, ok && inside);
+    if (!a.zero_init) {
+#pragma unroll
+      for (int q = 0; q < kQ; ++q)
+        cp_async<16>(slot + (R::kU + q) * 32 + lane, a.u_in, ro + 4 * q, a.bs, ok && inside);
     }
-    if (MODE == 6)
-      cp_async<16>(slot + R::kZB * 32 + lane, a.z, (size_t)((n >> 1) + 1) * a.pc + col, a.bs, ok && inside && (n & 1));
+    if (MODE == 3) {
+      // coarse nodes ca .. ca + kVec/2 - 1 of row n; lane 31 also takes node ca + kVec/2
+      const size_t zo = (size_t)n * a.pc + ca;
+      const bool zok = ok && col >= 0 && ca + kH <= a.pc;
+      if (kH == 4) cp_async<16>(slot + R::kZ * 32 + lane, a.z, zo, a.bs, zok);
+      else cp_async<8>(slot + R::kZ * 32 + lane, a.z, zo, a.bs, zok);
+      if (lane == 31) {
+        float* extra = reinterpret_cast<float*>(slot + (R::kZ + kH / 4) * 32 + lane) + kH % 4;
+        cp_async<4>(extra, a.z, zo + kH, a.bs, ok && col >= 0 && ca + kH < a.pc);
+      }
+    } else if (MODE == 4 || MODE == 6) {
+#pragma unroll
+      for (int q = 0; q < kQ; ++q)
+        cp_async<16>(slot + (R::kZ + q) * 32 + lane, a.z, (size_t)(n >> 1) * a.pc + col + 4 * q, a.bs, ok && inside);
+    }
+    if (MODE == 6) {
+#pragma unroll
+      for (int q = 0; q < kQ; ++q)
+        cp_async<16>(slot + (R::kZB + q) * 32 + lane, a.z, (size_t)((n >> 1) + 1) * a.pc + col + 4 * q, a.bs,
+                     ok && inside && (n & 1));
+    }
     if (!DOWN && a.u64 != nullptr) {
-      cp_async<16>(slot + R::k64 * 32 + lane, a.u64, ro, a.bs, ok && inside);
-      cp_async<16>(slot + (R::k64 + 1) * 32 + lane, a.u64, ro + 2, a.bs, ok && inside);
+#pragma unroll
+      for (int q = 0; q < 2 * kQ; ++q) cp_async<16>(slot + (R::k64 + q) * 32 + lane, a.u64, ro + 2 * q, a.bs, ok && inside);
     }
     cp_commit();
   };
 
   // One row: consume its ring slot, sweep, store, restrict.
-  auto row = [&](auto dir_tag, const int j, const Pipe<S>& in, Pipe<S>& out) {
+  auto row = [&](auto dir_tag, const int j, const Pipe<S, kVec>& in, Pipe<S, kVec>& out) {
     constexpr bool DIR = decltype(dir_tag)::value;
     const int n = first + j * step;
     const bool emit = n >= n0 && n < n1;
-    const float4* slot = &ring[w][j % kD][0][0];
+    const float4* slot = wring + (j % kD) * kSlot;
     cp_wait<kD - 1>();
-    const float4 b = slot[R::kB * 32 + lane];
-    float4 x = a.zero_init ? f4zero() : slot[R::kU * 32 + lane];
+    const V b = lds_v<kVec>(slot, R::kB, lane);
+    V x = a.zero_init ? vzero<kVec>() : lds_v<kVec>(slot, R::kU, lane);
     if (MODE == 3) {
-      // x-prolongation: fine 2j <- z_j, fine 2j+1 <- (z_j + z_{j+1}) / 2
-      const float4 zs = slot[R::kZ * 32 + lane];
-      float z2 = __shfl_down_sync(kFull, zs.x, 1);
-      if (lane == 31) z2 = zs.z;
-      x.x = fmaf(pm.x, zs.x, x.x);
-      x.y = fmaf(pm.y, 0.5f * (zs.x + zs.y), x.y);
-      x.z = fmaf(pm.z, zs.y, x.z);
-      x.w = fmaf(pm.w, 0.5f * (zs.y + z2), x.w);
+      // x-prolongation: fine 2q <- z_q, fine 2q+1 <- (z_q + z_{q+1}) / 2 (coarse node q of the lane)
+      const float* zs = reinterpret_cast<const float*>(slot + R::kZ * 32 + lane);
+      float zc[kH + 1];
+#pragma unroll
+      for (int q = 0; q < kH; ++q) zc[q] = zs[q];
+      const float* zx = reinterpret_cast<const float*>(slot + (R::kZ + kH / 4) * 32 + lane) + kH % 4;
+      const float zn = __shfl_down_sync(kFull, zc[0], 1);
+      zc[kH] = lane == 31 ? *zx : zn;
+#pragma unroll
+      for (int q = 0; q < kH; ++q) {
+        x.e[2 * q] = fmaf(pm.e[2 * q], zc[q], x.e[2 * q]);
+        x.e[2 * q + 1] = fmaf(pm.e[2 * q + 1], 0.5f * (zc[q] + zc[q + 1]), x.e[2 * q + 1]);
+      }
     } else if (MODE == 4 || MODE == 6) {
       // causal t-prolongation: fine rows 2m and 2m+1 <- coarse row m; bilinear: fine row
       // 2m+1 <- (z_m + z_{m+1}) / 2
-      float4 zz = slot[R::kZ * 32 + lane];
+      V zz = lds_v<kVec>(slot, R::kZ, lane);
       if (MODE == 6) {
-        const float4 zb = slot[R::kZB * 32 + lane];
-        const float4 zh = make_float4(0.5f * (zz.x + zb.x), 0.5f * (zz.y + zb.y), 0.5f * (zz.z + zb.z),
-                                      0.5f * (zz.w + zb.w));
-        zz = sel4(n & 1, zh, zz);
+        const V zb = lds_v<kVec>(slot, R::kZB, lane);
+        const bool odd = n & 1;
+#pragma unroll
+        for (int jj = 0; jj < kVec; ++jj) zz.e[jj] = odd ? 0.5f * (zz.e[jj] + zb.e[jj]) : zz.e[jj];
       }
-      x.x = fmaf(pm.x, zz.x, x.x);
-      x.y = fmaf(pm.y, zz.y, x.y);
-      x.z = fmaf(pm.z, zz.z, x.z);
-      x.w = fmaf(pm.w, zz.w, x.w);
+#pragma unroll
+      for (int jj = 0; jj < kVec; ++jj) x.e[jj] = fmaf(pm.e[jj], zz.e[jj], x.e[jj]);
     }
     out.v[0] = x;
 #pragma unroll
     for (int k = 1; k <= S; ++k) {
       if (k == 1 && a.zero_init) out.v[1] = b;  // a sweep from zero is exactly b'
       else
-        out.v[k] = stage<DIR>(a.omc, out.v[k - 1], in.v[k - 1], in.hl[k], in.hr[k], out.hl[k], out.hr[k], b, sl, su,
-                              spl, spc, spr);
+        out.v[k] = stage<DIR>(a.omc, out.v[k - 1], in.v[k - 1], in.hl[k], in.hr[k], out.hl[k], out.hr[k], b, cf);
     }
     if (!DOWN && a.u64 != nullptr) {
-      double2 lo = *reinterpret_cast<const double2*>(slot + R::k64 * 32 + lane);
-      double2 hi = *reinterpret_cast<const double2*>(slot + (R::k64 + 1) * 32 + lane);
-      lo.x += to_f64(out.v[S].x);
-      lo.y += to_f64(out.v[S].y);
-      hi.x += to_f64(out.v[S].z);
-      hi.y += to_f64(out.v[S].w);
+      double2 acc[kVec / 2];
+#pragma unroll
+      for (int q = 0; q < kVec / 2; ++q) {
+        acc[q] = *reinterpret_cast<const double2*>(slot + (R::k64 + q) * 32 + lane);
+        acc[q].x += to_f64(out.v[S].e[2 * q]);
+        acc[q].y += to_f64(out.v[S].e[2 * q + 1]);
+      }
       if (emit && owner) {
-        double2* q = reinterpret_cast<double2*>(a.u64 + (size_t)n * P + col);
-        q[0] = lo;
-        q[1] = hi;
+        double2* dst = reinterpret_cast<double2*>(a.u64 + (size_t)n * P + col);
+#pragma unroll
+        for (int q = 0; q < kVec / 2; ++q) dst[q] = acc[q];
       }
     } else if (emit && owner) {
-      *reinterpret_cast<float4*>(a.u_out + (size_t)n * P + col) = out.v[S];
+      stg_v(a.u_out + (size_t)n * P + col, out.v[S]);
     }
     if (DOWN) {
       // scaled residual y = b' - omega u + sum S_k u_k, r = (D / omega) y
-      const float4 y = stage<DIR>(-a.omega, out.v[S], in.v[S], in.hl[S + 1], in.hr[S + 1], out.hl[S + 1], out.hr[S + 1], b,
-                                  sl, su, spl, spc, spr);
-      const float4 r = DIR ? make_float4(a.Wo * y.x, a.Wo * y.y, a.Wo * y.z, a.Wo * y.w) : mul4(dw, y);
+      const V y =
+          stage<DIR>(-a.omega, out.v[S], in.v[S], in.hl[S + 1], in.hr[S + 1], out.hl[S + 1], out.hr[S + 1], b, cf);
+      V r;
+#pragma unroll
+      for (int jj = 0; jj < kVec; ++jj) r.e[jj] = (DIR ? a.Wo : dw.e[jj]) * y.e[jj];
       out.r = r;
       if (MODE == 5) out.rp = in.r;
       if (MODE == 1) {
         // b_c[j] = r[2j] + (r[2j-1] + r[2j+1]) / 2, scaled by omega / D_c
-        const float rl = __shfl_up_sync(kFull, r.w, 1);
-        const float s0 = DIR ? a.cwW : sx0;
-        const float s1 = DIR ? a.cwW : cwx.y;
-        const float2 o = make_float2(s0 * (r.x + 0.5f * (rl + r.y)), s1 * (r.z + 0.5f * (r.y + r.w)));
-        float* dst = a.bc + (size_t)n * a.pc + col / 2;
-        if (emit && own0) dst[0] = o.x;
-        if (emit && own1) dst[1] = o.y;
+        const float rl = __shfl_up_sync(kFull, r.e[kVec - 1], 1);
+        float* dst = a.bc + (size_t)n * a.pc + ca;
+#pragma unroll
+        for (int q = 0; q < kH; ++q) {
+          const float left = q == 0 ? rl : r.e[2 * q - 1];
+          const float s = DIR ? a.cwW : cwx[q];
+          const float o = s * (r.e[2 * q] + 0.5f * (left + r.e[2 * q + 1]));
+          if (emit && owner && col + 2 * q <= a.N) dst[q] = o;
+        }
       } else {
-        float4 sum;
+        V sum;
         int m;
         bool put;
         const bool odd = n & 1;
         if (MODE == 2) {
           // b_c[m] = (r[2m] + r[2m+1]) / 2 (causal P^T with s = 1/2); forward: emitted at
           // row 2m+1 (row NT alone when NT is even); J^T: emitted at row 2m
-          if (!ADJ) {
-            sum = odd ? make_float4(r.x + in.r.x, r.y + in.r.y, r.z + in.r.z, r.w + in.r.w) : r;
-            put = emit && (odd || n == a.NT);
-          } else {
-            sum = make_float4(r.x + in.r.x, r.y + in.r.y, r.z + in.r.z, r.w + in.r.w);
-            put = emit && !odd;
-          }
+#pragma unroll
+          for (int jj = 0; jj < kVec; ++jj) sum.e[jj] = (ADJ || odd) ? r.e[jj] + in.r.e[jj] : r.e[jj];
+          put = ADJ ? (emit && !odd) : (emit && (odd || n == a.NT));
           m = n >> 1;
         } else {
           // b_c[m] = (r[2m] + (r[2m-1] + r[2m+1]) / 2) / 2 (bilinear P^T with s = 1/2),
           // emitted when the last of its three fine rows has been processed
-          const float4 so = make_float4(in.r.x + 0.5f * (in.rp.x + r.x), in.r.y + 0.5f * (in.rp.y + r.y),
-                                        in.r.z + 0.5f * (in.rp.z + r.z), in.r.w + 0.5f * (in.rp.w + r.w));
-          const float4 se = make_float4(r.x + 0.5f * in.r.x, r.y + 0.5f * in.r.y, r.z + 0.5f * in.r.z,
-                                        r.w + 0.5f * in.r.w);
-          sum = sel4(odd, so, se);
+#pragma unroll
+          for (int jj = 0; jj < kVec; ++jj)
+            sum.e[jj] = odd ? in.r.e[jj] + 0.5f * (in.rp.e[jj] + r.e[jj]) : r.e[jj] + 0.5f * in.r.e[jj];
           if (!ADJ) {
             const int nm = n - 1;
             m = odd ? nm >> 1 : n >> 1;
@@ -333,20 +405,21 @@ __global__ void __launch_bounds__(kThreads, 4) k_stream(StreamArgs a) {
             put = odd ? (np >= n0 && np < n1) : (emit && n == 0);
           }
         }
-        const float4 sc = sel4(m == 0, cwW4, cwt);
-        const float4 o = make_float4(0.5f * sc.x * sum.x, 0.5f * sc.y * sum.y, 0.5f * sc.z * sum.z, 0.5f * sc.w * sum.w);
-        if (put && owner) *reinterpret_cast<float4*>(a.bc + (size_t)m * a.pc + col) = o;
+        V o;
+#pragma unroll
+        for (int jj = 0; jj < kVec; ++jj) o.e[jj] = 0.5f * (m == 0 ? a.cwW : cwt.e[jj]) * sum.e[jj];
+        if (put && owner) stg_v(a.bc + (size_t)m * a.pc + col, o);
       }
     }
   };
 
-  Pipe<S> A, B;
+  Pipe<S, kVec> A, B;
 #pragma unroll
-  for (int k = 0; k <= S; ++k) A.v[k] = f4zero();
+  for (int k = 0; k <= S; ++k) A.v[k] = vzero<kVec>();
 #pragma unroll
   for (int k = 0; k <= S + 1; ++k) A.hl[k] = A.hr[k] = 0.f;
-  A.r = f4zero();
-  A.rp = f4zero();
+  A.r = vzero<kVec>();
+  A.rp = vzero<kVec>();
 #pragma unroll
   for (int j = 0; j < kD; ++j) fetch(j);
   int j = 0;
@@ -383,7 +456,8 @@ cudaError_t launch_k(const StreamArgs& a0, cudaStream_t s) {
   static std::atomic<int> resident{0};
   int nb = resident.load(std::memory_order_relaxed);
   if (nb == 0) {
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stream<ADJ, S, MODE>, kThreads, 0);
+    cudaError_t e =
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stream<ADJ, S, MODE>, Width<MODE>::kThreads, 0);
     if (e != cudaSuccess) return e;
     nb = nb < 1 ? 1 : nb;
     resident.store(nb, std::memory_order_relaxed);
@@ -393,10 +467,11 @@ cudaError_t launch_k(const StreamArgs& a0, cudaStream_t s) {
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
   StreamArgs a = a0;
-  stream_layout(a.N, a.NT, (long long)nb * kWarpsPerBlock * sms, a);
+  constexpr int wpb = Width<MODE>::kWarpsPerBlock;
+  stream_layout(a.N, a.NT, Width<MODE>::kOwn, (long long)nb * wpb * sms, a);
   const long long warps = (long long)a.strips * a.chunks;
-  const unsigned grid = (unsigned)((warps + kWarpsPerBlock - 1) / kWarpsPerBlock);
-  k_stream<ADJ, S, MODE><<<grid, kThreads, 0, s>>>(a);
+  const unsigned grid = (unsigned)((warps + wpb - 1) / wpb);
+  k_stream<ADJ, S, MODE><<<grid, Width<MODE>::kThreads, 0, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -414,8 +489,8 @@ cudaError_t launch_mode(const StreamArgs& a, int S, cudaStream_t s) {
 
 }  // namespace
 
-void stream_layout(int N, int NT, long long resident_warps, StreamArgs& a) {
-  a.strips = (N + 1 + kOwn - 1) / kOwn;
+void stream_layout(int N, int NT, int own, long long resident_warps, StreamArgs& a) {
+  a.strips = (N + 1 + own - 1) / own;
   // one wave: about one chunk per resident warp, chunks of an even number of rows in
   // [4, 1024].  A chunk re-computes S + 1 warm-up rows, which costs little on the large
   // levels (hundreds of rows per chunk) and nothing on the small ones, where short chunks

@@ -34,9 +34,9 @@ struct StreamArgs {
   int rows, strips, chunks;
 };
 
-// Fills rows / strips / chunks for a level of N elements and NT steps so that one wave of
-// resident_warps warps covers it.
-void stream_layout(int N, int NT, long long resident_warps, StreamArgs& a);
+// Fills rows / strips / chunks for a level of N elements and NT steps, windows owning `own`
+// columns, so that one wave of resident_warps warps covers it.
+void stream_layout(int N, int NT, int own, long long resident_warps, StreamArgs& a);
 // S sweeps (1..5) in one pass of the given mode; adj selects J^T.
 cudaError_t launch_stream(int mode, bool adj, int S, const StreamArgs& a, cudaStream_t s);
 
