@@ -112,6 +112,28 @@ __device__ __forceinline__ double to_f64(float f) {
   return __hiloint2double((int)hi, (int)lo);
 }
 
+// Programmatic dependent launch (sm_90 and later): a kernel launched with launch_pdl may
+// start while the previous kernel of its stream drains; it calls pdl_wait() before its first
+// access to memory that earlier kernels write, which also lets the next such kernel launch.
+// Launched the ordinary way, a kernel's pdl_wait() returns at once.
+__device__ __forceinline__ void pdl_wait() {
+  asm volatile("griddepcontrol.wait;\n" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // Sets the message returned by stmg_last_error(NULL) on this host thread.
 void set_global_error(const char* msg);
 

@@ -233,6 +233,7 @@ template <typename T>
 __global__ void __launch_bounds__(32) k_exact(ThomasView tv, bool adj, const T* __restrict__ b, T* __restrict__ u) {
   const int N = tv.N, NT = tv.NT, P = tv.pitch;
   const int lane = threadIdx.x;
+  pdl_wait();
   for (int i = lane; i <= N; i += 32) u[i] = (T)((double)b[i] / tv.omega);
   for (int n = 1 + lane; n <= NT; n += 32) u[(size_t)n * P] = (T)((double)b[(size_t)n * P] / tv.omega);
   const int i0 = 2 * lane + 1, i1 = 2 * lane + 2;
@@ -638,9 +639,8 @@ cudaError_t launch_prolong_add(int type, int Nf, int NTf, int pf, T* u, int Nc, 
 template <typename T>
 cudaError_t launch_exact(const ThomasView& tv, bool adj, const T* b, T* u, cudaStream_t s) {
   if (tv.N < 1 || tv.N > kExactWarpMaxN) return cudaErrorInvalidValue;
-  k_exact<T><<<1, 32, 0, s>>>(tv, adj, b, u);
   count_launches(1);
-  return cudaGetLastError();
+  return launch_pdl(k_exact<T>, dim3(1), dim3(32), s, tv, adj, b, u);
 }
 
 cudaError_t launch_design_update(int N, const double* chi, const double* g, double vol, double move, double* out,

@@ -420,6 +420,10 @@ __global__ void __launch_bounds__(Width<MODE>::kThreads, Width<MODE>::kMinBlocks
   for (int k = 0; k <= S + 1; ++k) A.hl[k] = A.hr[k] = 0.f;
   A.r = vzero<kVec>();
   A.rp = vzero<kVec>();
+  // Everything above reads only the level's coefficients, fixed since the hierarchy was
+  // built.  The rows come from the kernels before this one: wait for them (a no-op unless
+  // this grid was launched ahead of its predecessor's end) and let the next pass launch.
+  pdl_wait();
 #pragma unroll
   for (int j = 0; j < kD; ++j) fetch(j);
   int j = 0;
@@ -471,8 +475,9 @@ cudaError_t launch_k(const StreamArgs& a0, cudaStream_t s) {
   stream_layout(a.N, a.NT, Width<MODE>::kOwn, (long long)nb * wpb * sms, a);
   const long long warps = (long long)a.strips * a.chunks;
   const unsigned grid = (unsigned)((warps + wpb - 1) / wpb);
-  k_stream<ADJ, S, MODE><<<grid, Width<MODE>::kThreads, 0, s>>>(a);
-  return cudaGetLastError();
+  // programmatic dependent launch: the pass may start (and load its coefficients) while the
+  // previous kernel of the stream drains; it waits for that kernel before touching any row
+  return launch_pdl(k_stream<ADJ, S, MODE>, dim3(grid), dim3(Width<MODE>::kThreads), s, a);
 }
 
 template <bool ADJ, int MODE>
