@@ -246,7 +246,7 @@ def workload_opts(w):
     return {"nu": w["nu"]} if "nu" in w else {}
 
 
-SERVING_OPTS = dict(precision="mixed", tol=TOL, nu=20, max_cycles=300)
+SERVING_OPTS = dict(precision="mixed", tol=TOL, nu=60, max_cycles=300)
 
 
 def run_serving(nreq, workers, inner=3, compare=8):
