@@ -46,6 +46,9 @@ struct Level {
   double* dgco = nullptr;
   double* dgwd = nullptr;
   double* dglu[2] = {nullptr, nullptr};
+  // narrow coarsest level: powers G^(2^k), k < npw, of G = -A^-1 B for the scan in time
+  double* dpw = nullptr;
+  int npw = 0;
 };
 
 }  // namespace
@@ -157,6 +160,8 @@ void free_level(stmg_t h, Level& L) {
   dfree(h, L.dk); dfree(h, L.dc); dfree(h, L.cf64); dfree(h, L.cf32); dfree(h, L.th);
   dfree(h, L.u); dfree(h, L.b); dfree(h, L.t); dfree(h, L.u32); dfree(h, L.b32); dfree(h, L.t32);
   dfree(h, L.dcls); dfree(h, L.dgco); dfree(h, L.dgwd); dfree(h, L.dglu[0]); dfree(h, L.dglu[1]);
+  dfree(h, L.dpw);
+  L.npw = 0;
 }
 
 bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
@@ -439,6 +444,7 @@ inline int transfer_type(const stmg_opts& o, const Level& L) {
 template <typename T>
 cudaError_t exact_level(stmg_t h, const Level& L, bool adj, const T* bs, T* u) {
   if (L.gal) return gal_exact<T>(L, adj, bs, u, h->s);
+  if (L.dpw) return launch_exact_scan<T>(thomas_view(L, h->o.omega), adj, L.npw, L.dpw, bs, u, h->s);
   if (L.N > 64) return launch_exact_par<T>(slab_view(L, h->o.omega, L.NT), adj, bs, u, h->s);
   return launch_exact<T>(thomas_view(L, h->o.omega), adj, bs, u, h->s);
 }
@@ -473,7 +479,11 @@ stmg_status vcycle(stmg_t h, int l, bool adj, bool zero_init, bool first_done) {
   int pre = h->o.nu;
   if (zero_init && !first_done) {
     Vecs<T> v = vecs<T>(L);
-    if (pre > 0 && !L.gal) {  // (a Galerkin level keeps b unscaled: it sweeps from 0 instead)
+    if (pre >= 2 && !L.gal) {
+      // the first sweep from 0 is exactly b'; the second reads b' in its place
+      CK(launch_sweep<T>(view<T>(L, h->o.omega), adj, v.b, v.b, v.u, h->s));
+      pre -= 2;
+    } else if (pre > 0 && !L.gal) {  // (a Galerkin level keeps b unscaled: it sweeps from 0 instead)
       CK(cudaMemcpyAsync(v.u, v.b, L.nvec * sizeof(T), cudaMemcpyDeviceToDevice, h->s));
       --pre;
     } else {
@@ -913,6 +923,50 @@ stmg_status build_galerkin(stmg_t h) {
   return STMG_OK;
 }
 
+// The coarsest level, when narrow and short enough, is solved by a scan in time (see
+// k_exact_scan): G = -A^-1 B from its Thomas factors and G^(2^k) for 2^K >= NT.
+stmg_status build_scan_powers(stmg_t h) {
+  Level& Z = h->lev.back();
+  dfree(h, Z.dpw);
+  Z.npw = 0;
+  const int N = Z.N, NT = Z.NT;
+  if (Z.gal || N < 1 || N > 64 || NT < 2 || (long long)NT * N > 8192) return STMG_OK;
+  int K = 0;
+  while ((1 << K) < NT) ++K;
+  if ((long long)K * NT * N * N > (1LL << 20)) return STMG_OK;
+  std::vector<double> th;
+  thomas_factors(Z, th);
+  const size_t S = N + 2;
+  const double *lo = &th[0], *inv = &th[S], *cp = &th[2 * S], *pl = &th[3 * S], *pc = &th[4 * S], *pr = &th[5 * S];
+  std::vector<double> pw((size_t)K * N * N), x(S);
+  double* G = pw.data();
+  for (int J = 1; J <= N; ++J) {  // column J of B: rows J-1 (pr), J (pc), J+1 (pl)
+    double dp = 0.0;
+    for (int i = 1; i <= N; ++i) {
+      const double bij = i == J ? pc[i] : (i == J + 1 ? pl[i] : (i + 1 == J ? pr[i] : 0.0));
+      dp = (bij - lo[i] * dp) * inv[i];
+      x[i] = dp;
+    }
+    for (int i = N - 1; i >= 1; --i) x[i] -= cp[i] * x[i + 1];
+    for (int i = 1; i <= N; ++i) G[(size_t)(i - 1) * N + (J - 1)] = -x[i];
+  }
+  for (int k = 1; k < K; ++k) {
+    const double* A = pw.data() + (size_t)(k - 1) * N * N;
+    double* C = pw.data() + (size_t)k * N * N;
+    for (int i = 0; i < N; ++i)
+      for (int j = 0; j < N; ++j) {
+        double acc = 0.0;
+        for (int m = 0; m < N; ++m) acc += A[(size_t)i * N + m] * A[(size_t)m * N + j];
+        C[(size_t)i * N + j] = acc;
+      }
+  }
+  CKS(dalloc(h, &Z.dpw, pw.size()));
+  CK(cudaMemcpyAsync(Z.dpw, pw.data(), pw.size() * sizeof(double), cudaMemcpyHostToDevice, h->s));
+  CK(cudaStreamSynchronize(h->s));  // pw must outlive the copy
+  Z.npw = K;
+  return STMG_OK;
+}
+
 stmg_status build_hierarchy(stmg_t h, const std::vector<double>& hk, const std::vector<double>& hc) {
   reset_graphs(h);
   std::vector<Level> nl = plan_levels(h->o, h->N, h->NT, h->L, h->tT, hk.data(), hc.data(),
@@ -932,6 +986,7 @@ stmg_status build_hierarchy(stmg_t h, const std::vector<double>& hk, const std::
   for (Level& L : h->lev) CKS(setup_level(h, L));
   CKS(alloc_vectors(h));
   CKS(build_galerkin(h));
+  CKS(build_scan_powers(h));
   CK(cudaStreamSynchronize(h->s));
   return STMG_OK;
 }

@@ -168,6 +168,12 @@ cudaError_t launch_prolong_add(int type, int Nf, int NTf, int pf, T* u, int Nc, 
 // Exact solve of J u = b from the stored b'.
 template <typename T>
 cudaError_t launch_exact(const ThomasView& tv, bool adj, const T* bs, T* u, cudaStream_t s);
+// The same solve for narrow levels as a scan in time with the precomputed powers
+// pw[k] = G^(2^k), k < K, of G = -A^-1 B (N x N, row-major); needs 2 NT N doubles of shared
+// memory.
+template <typename T>
+cudaError_t launch_exact_scan(const ThomasView& tv, bool adj, int K, const double* pw, const T* bs, T* u,
+                              cudaStream_t s);
 // x <- (omega/D) x (to_scaled) or (D/omega) x over a level vector, in place.
 template <typename T>
 cudaError_t launch_scale(const LevelView<T>& lv, bool to_scaled, T* x, cudaStream_t s);

@@ -318,6 +318,61 @@ __global__ void __launch_bounds__(32) k_exact(ThomasView tv, bool adj, const T* 
   }
 }
 
+// Exact solve of a narrow coarsest level by a scan in time.  With the Dirichlet columns
+// eliminated, the interior rows of J u = b read A u_n = b_n - B u_{n-1} (n >= 2; row 1 has
+// no coupling to the Dirichlet row 0), with A = (M/dt + K)_int and B = -(M/dt)_int, and
+// those of J^T u = b read A u_n = b_n - B u_{n+1} (n <= NT - 1), B being symmetric.  So
+// u_n = f_n + G u_{n-+1} with f_n = A^-1 b_n and G = -A^-1 B in both directions.  The f_n
+// are independent tridiagonal solves (Thomas, one row per thread); the recurrence is a
+// Kogge-Stone scan over n, whose step with distance 2^k multiplies by G^(2^k), precomputed
+// on the host (pw: K row-major N x N matrices).  One block; the rows live in shared memory
+// (two buffers of NT x N doubles).  Arithmetic in FP64 whatever the storage type.
+template <typename T>
+__global__ void __launch_bounds__(256) k_exact_scan(ThomasView tv, bool adj, int K, const double* __restrict__ pw,
+                                                    const T* __restrict__ b, T* __restrict__ u) {
+  extern __shared__ double sm[];
+  const int N = tv.N, NT = tv.NT, P = tv.pitch;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  pdl_wait();
+  for (int i = tid; i <= N; i += nth) u[i] = (T)((double)b[i] / tv.omega);
+  for (int n = 1 + tid; n <= NT; n += nth) u[(size_t)n * P] = (T)((double)b[(size_t)n * P] / tv.omega);
+  double* g = sm;                    // row n (1..NT), node i (1..N) at (n - 1) * N + i - 1
+  double* h = sm + (size_t)NT * N;
+  for (int n = 1 + tid; n <= NT; n += nth) {
+    double* f = g + (size_t)(n - 1) * N - 1;  // f[i], i = 1..N
+    const T* bn = b + (size_t)n * P;
+    double dp = 0.0;
+    for (int i = 1; i <= N; ++i) {
+      dp = ((double)bn[i] * tv.dw[i] - tv.lo[i] * dp) * tv.inv[i];
+      f[i] = dp;
+    }
+    for (int i = N - 1; i >= 1; --i) f[i] -= tv.cp[i] * f[i + 1];
+  }
+  __syncthreads();
+  for (int k = 0, d = 1; k < K; ++k, d <<= 1) {
+    const double* Gk = pw + (size_t)k * N * N;
+    for (int q = tid; q < NT * N; q += nth) {
+      const int n = 1 + q / N, i = q - (n - 1) * N;
+      const int m = adj ? n + d : n - d;
+      double v = g[q];
+      if (adj ? m <= NT : m >= 1) {
+        const double* src = g + (size_t)(m - 1) * N;
+        const double* row = Gk + (size_t)i * N;
+        for (int j = 0; j < N; ++j) v = fma(row[j], src[j], v);
+      }
+      h[q] = v;
+    }
+    __syncthreads();
+    double* t = g;
+    g = h;
+    h = t;
+  }
+  for (int q = tid; q < NT * N; q += nth) {
+    const int n = 1 + q / N, i = q - (n - 1) * N;
+    u[(size_t)n * P + 1 + i] = (T)g[q];
+  }
+}
+
 // One projected-gradient design update, the stand-in for the MMA optimiser of the
 // optimisation loop (Sec. 7.2): y = chi - move * (g / max|g|) and
 // chi_new = clamp(y - mu, max(0, chi - move), min(1, chi + move)), mu >= 0 the smallest
@@ -637,6 +692,28 @@ cudaError_t launch_prolong_add(int type, int Nf, int NTf, int pf, T* u, int Nc, 
 }
 
 template <typename T>
+cudaError_t launch_exact_scan(const ThomasView& tv, bool adj, int K, const double* pw, const T* b, T* u,
+                              cudaStream_t s) {
+  const size_t smem = 2 * sizeof(double) * (size_t)tv.NT * tv.N;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_exact_scan<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(1);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  count_launches(1);
+  return cudaLaunchKernelEx(&cfg, k_exact_scan<T>, tv, adj, K, pw, b, u);
+}
+
+template <typename T>
 cudaError_t launch_exact(const ThomasView& tv, bool adj, const T* b, T* u, cudaStream_t s) {
   if (tv.N < 1 || tv.N > kExactWarpMaxN) return cudaErrorInvalidValue;
   count_launches(1);
@@ -739,6 +816,7 @@ cudaError_t launch_sens_final(int N, int chunks, const double* chi, Simp6 sp, co
   template cudaError_t launch_restrict<T>(int, int, int, int, const T*, const LevelView<T>&, T*, cudaStream_t);   \
   template cudaError_t launch_prolong_add<T>(int, int, int, int, T*, int, int, int, const T*, cudaStream_t);      \
   template cudaError_t launch_exact<T>(const ThomasView&, bool, const T*, T*, cudaStream_t);                      \
+  template cudaError_t launch_exact_scan<T>(const ThomasView&, bool, int, const double*, const T*, T*, cudaStream_t); \
   template cudaError_t launch_scale<T>(const LevelView<T>&, bool, T*, cudaStream_t);                              \
   template cudaError_t launch_resnorm<T>(const LevelView<T>&, bool, const T*, const T*, double*, double*,         \
                                          cudaStream_t);

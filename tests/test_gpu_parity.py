@@ -159,6 +159,39 @@ def test_fp32_cycle_matches_oracle_cycle(i, adj, nu):
     g.close()
 
 
+@pytest.mark.parametrize("N", [236, 240, 244, 480, 484, 728])
+@pytest.mark.parametrize("adj", [False, True])
+def test_fp32_cycle_at_window_boundaries(N, adj):
+    """The fused passes split a level into windows of 240 (DOWN, 8 columns per lane) and
+    112 (UP, 4 per lane) owned columns: widths on both sides of one, two and three windows,
+    with several x-coarsenings below, against the oracle's FP64 cycle from zero."""
+    NT = 48
+    k, c = _rand_material(300 + N, N, 1e3)
+    deff = np.sqrt((k / c).min() * (k / c).max())
+    tT = 3.0 * (1.0 / N) ** 2 / deff * NT
+    g, o = _pair(N, NT, 1.0, tT, k, c, max_coarse_dofs=64, precision="mixed")
+    assert o.path().count("x") >= 2
+    b = _rand_vec(7, o.shape(0))
+    ug = np.zeros(o.shape(0))
+    g.vcycle(ug, b, adjoint=adj)
+    assert rel(ug, o.vcycle(np.zeros(o.shape(0)), b, adj=adj)) < 2e-4
+    g.close()
+
+
+def test_mixed_single_level_and_tiny_grids():
+    """No coarsening (a one-level hierarchy) and grids narrower than one lane's columns."""
+    for N, NT in ((1, 1), (3, 5), (6, 10)):
+        k, c = _rand_material(400 + N, N, 10.0)
+        g, o = _pair(N, NT, 1.0, 1.0, k, c, max_coarse_dofs=1, precision="mixed", tol=1e-8)
+        b = _rand_vec(8, o.shape(0))
+        u = np.empty(o.shape(0))
+        st, cyc, rr = g.solve(u, b=b)
+        assert st == "ok" and rr < 1e-8
+        ue = oracle.exact(N, NT, 1.0, 1.0, k, c, b)
+        assert rel(u, ue) < 1e-6
+        g.close()
+
+
 @pytest.mark.parametrize("i", [1, 2, 3])
 @pytest.mark.parametrize("adj", [False, True])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
