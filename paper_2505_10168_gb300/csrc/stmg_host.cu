@@ -439,8 +439,9 @@ inline int transfer_type(const stmg_opts& o, const Level& L) {
   return L.next == STMG_TCOARSEN && o.interp == STMG_INTERP_BILINEAR ? 3 : L.next;
 }
 
-// Exact solve on one level: one thread runs the recurrences for narrow levels, a block-wide
-// scan for wider ones.
+// Exact solve on one level: the block LU of a Galerkin level; a scan over the time rows for
+// a narrow, short coarsest level; one warp per step (the Thomas recurrences as warp scans)
+// for other narrow levels; block-wide scans per step for wider ones.
 template <typename T>
 cudaError_t exact_level(stmg_t h, const Level& L, bool adj, const T* bs, T* u) {
   if (L.gal) return gal_exact<T>(L, adj, bs, u, h->s);

@@ -8,6 +8,15 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 
+def pytest_sessionstart(session):
+    """The compiled library is not versioned: build it when it is missing or older than its
+    sources (nvcc cross-compiles for sm_103a without a GPU), so the CPU suite runs from a
+    clean checkout."""
+    from paper_2505_10168_gb300 import build_lib
+
+    build_lib.build()
+
+
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (sm_103a) and the compiled library")
     config.addinivalue_line("markers", "slow: long-running CPU test")
