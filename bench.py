@@ -251,7 +251,8 @@ SERVING_OPTS = dict(precision="mixed", tol=TOL, nu=60, max_cycles=300)
 
 def run_serving(nreq, workers, inner=3, compare=8):
     """Closed loop (all requests queued at once) for throughput, then the same requests
-    with their Poisson gaps rescaled to 0.8x that throughput for latency."""
+    with their Poisson gaps rescaled to 0.5x, 0.8x and 1.0x that throughput for latency
+    (0.8x is the headline p50/p99)."""
     from paper_2505_10168_gb300 import serving as sv
     from paper_2505_10168_gb300 import workloads as wl
 
@@ -263,8 +264,10 @@ def run_serving(nreq, workers, inner=3, compare=8):
         _, closed = sv.replay(srv, reqs, fields, speed=1e9, **opts)
         rate = closed["requests"] / closed["makespan_s"]  # requests per second
         mean_gap = (reqs[-1]["arrival"] - reqs[0]["arrival"]) / max(1, len(reqs) - 1)
-        speed = 0.8 * rate * mean_gap
-        _, poisson = sv.replay(srv, reqs, fields, speed=speed, **opts)
+        loads = {}
+        for load in (0.5, 0.8, 1.0):  # Poisson arrivals at this fraction of that rate
+            _, loads[load] = sv.replay(srv, reqs, fields, speed=load * rate * mean_gap, **opts)
+        poisson = loads[0.8]
         # the same first requests, mixed and batched, against the plain FP64 single-solve
         # form: FP64 V-cycles, one request at a time (one worker), same tolerance and cap
         sub = reqs[: min(compare, nreq)]
@@ -277,6 +280,7 @@ def run_serving(nreq, workers, inner=3, compare=8):
           "speedup": batched["dofs_per_s"] / single["dofs_per_s"] if single["dofs_per_s"] > 0 else None}
     return {"requests": nreq, "of": 512, "workers": workers, "solver": opts,
             "closed_loop": closed, "poisson_0.8": poisson,
+            "p50_p99_by_load": {str(l): [v["p50_s"], v["p99_s"]] for l, v in loads.items()},
             "p50_s": poisson["p50_s"], "p99_s": poisson["p99_s"], "dofs_per_s": closed["dofs_per_s"],
             "vs_fp64_single": vs}
 
