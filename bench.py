@@ -46,6 +46,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-variant", action="store_true", help="skip the other-precision solve of the same workload")
     p.add_argument("--mixed-inner", type=int, default=3, help="FP32 V-cycles per FP64 defect in the mixed scheme")
+    p.add_argument("--mixed-first", type=int, default=3, help="FP32 V-cycles on the first defect in the mixed scheme")
     p.add_argument("--serving-requests", type=int, default=64,
                    help="requests of the 512-request serving trace to replay (0: skip serving)")
     p.add_argument("--serving-workers", type=int, default=6)
@@ -238,7 +239,9 @@ def whole_job_rate(units_per_rank, world, seconds):
 # ----------------------------------------------------------------------------- serving
 def precision_opts(args, precision):
     """Solver options that only the mixed scheme takes."""
-    return {"mixed_inner_cycles": args.mixed_inner} if precision == "mixed" else {}
+    if precision != "mixed":
+        return {}
+    return {"mixed_inner_cycles": args.mixed_inner, "mixed_first_cycles": args.mixed_first}
 
 
 def workload_opts(w):
