@@ -779,7 +779,7 @@ stmg_status solve_loop(stmg_t h, bool adj, bool warm, int* cycles_out, double* r
     // the first sweep of cycle 1 (with the norm of the starting iterate if it is not 0)
     if (!one_level && o.nu > 0) {
       if (warm) {
-        CK(launch_sweep_norm<double>(lv, adj, L.u, L.b, L.t, h->partials, h->scal, h->s));
+        CK(launch_sweep_norm<double>(lv, adj, L.u, L.b, L.t, L.cf32 + (size_t)kDW * L.pitch, h->partials, h->scal, h->s));
         CKS(read_scalar(h, h->scal, &r2));
       } else {
         CK(cudaMemcpyAsync(L.t, L.b, L.nvec * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
@@ -801,7 +801,7 @@ stmg_status solve_loop(stmg_t h, bool adj, bool warm, int* cycles_out, double* r
           CKS(capture_graph(h, &gx, &gk, [&]() -> stmg_status {
             std::swap(L.u, L.t);
             CKS(vcycle<double>(h, 0, adj, false, true));
-            CK(launch_sweep_norm<double>(lv, adj, L.u, L.b, L.t, h->partials, h->scal, h->s));
+            CK(launch_sweep_norm<double>(lv, adj, L.u, L.b, L.t, L.cf32 + (size_t)kDW * L.pitch, h->partials, h->scal, h->s));
             return STMG_OK;
           }));
           if (L.u != u_before) return fail(h, STMG_ECUDA, "internal: odd number of level-0 swaps in a cycle");

@@ -148,10 +148,11 @@ constexpr int kNormBlocks = 608;  // 4 x 152 SMs: fixed grid of every reduction
 template <typename T>
 cudaError_t launch_sweep(const LevelView<T>& lv, bool adj, const T* u, const T* bs, T* uo, cudaStream_t s);
 // The same sweep, also writing the partial sums of ||b - J u||^2 (u = the input iterate)
-// into partials[kNormBlocks]; then out[0] = the total.  Deterministic.
+// into partials[kNormBlocks]; then out[0] = the total.  Deterministic.  dw32: the level's
+// FP32 D / omega (the norm is accumulated in FP32 per thread).
 template <typename T>
-cudaError_t launch_sweep_norm(const LevelView<T>& lv, bool adj, const T* u, const T* bs, T* uo, double* partials,
-                              double* out, cudaStream_t s);
+cudaError_t launch_sweep_norm(const LevelView<T>& lv, bool adj, const T* u, const T* bs, T* uo, const float* dw32,
+                              double* partials, double* out, cudaStream_t s);
 // r = b - J u from the stored b'.
 template <typename T>
 cudaError_t launch_residual(const LevelView<T>& lv, bool adj, const T* u, const T* bs, T* r, cudaStream_t s);

@@ -113,21 +113,30 @@ __device__ __forceinline__ double block_sum(double v) {
 }
 
 // Sweep that also accumulates ||b - J u||^2 of the input iterate (fixed grid, grid-stride).
+// The sweep's increment y = uo - u is the scaled residual (omega / D)(b - J u), exact in T;
+// the norm only decides termination, so r = (D / omega) y is formed and squared in FP32 per
+// thread (y truncated by its bit fields, dw32 = the FP32 copy of D / omega) and summed in
+// FP64 across the block: in FP64 the kernel costs 7 operations per DOF, a plain sweep 6.
 template <typename T, bool ADJ>
 __global__ void __launch_bounds__(kThreads) k_sweep_norm(LevelView<T> lv, uint32_t total, const T* __restrict__ u,
                                                          const T* __restrict__ bs, T* __restrict__ uo,
+                                                         const float* __restrict__ dw32,
                                                          double* __restrict__ partials) {
-  double acc = 0.0;
+  float acc = 0.f;
+  const float Wo32 = (float)lv.Wo;
   for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
     int n, i;
     split_index(idx, lv.fd, n, i);
     const size_t p = (size_t)n * lv.pitch + i;
     const T y = scaled_residual<T, ADJ>(lv, u, bs, n, i, p);
     uo[p] = u[p] + y;
-    const double r = (double)(unscale(lv, n, i) * y);
-    acc = fma(r, r, acc);
+    float yf;
+    if constexpr (std::is_same<T, double>::value) yf = to_f32_trunc(y);
+    else yf = y;
+    const float r = ((n == 0 || i == 0) ? Wo32 : dw32[i]) * yf;
+    acc = fmaf(r, r, acc);
   }
-  const double s = block_sum<kThreads>(acc);
+  const double s = block_sum<kThreads>((double)acc);
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
@@ -643,11 +652,11 @@ cudaError_t launch_sweep(const LevelView<T>& lv, bool adj, const T* u, const T* 
 }
 
 template <typename T>
-cudaError_t launch_sweep_norm(const LevelView<T>& lv, bool adj, const T* u, const T* bs, T* uo, double* partials,
-                              double* out, cudaStream_t s) {
+cudaError_t launch_sweep_norm(const LevelView<T>& lv, bool adj, const T* u, const T* bs, T* uo, const float* dw32,
+                              double* partials, double* out, cudaStream_t s) {
   const uint32_t n = dofs(lv);
-  if (adj) k_sweep_norm<T, true><<<kNormBlocks, kThreads, 0, s>>>(lv, n, u, bs, uo, partials);
-  else k_sweep_norm<T, false><<<kNormBlocks, kThreads, 0, s>>>(lv, n, u, bs, uo, partials);
+  if (adj) k_sweep_norm<T, true><<<kNormBlocks, kThreads, 0, s>>>(lv, n, u, bs, uo, dw32, partials);
+  else k_sweep_norm<T, false><<<kNormBlocks, kThreads, 0, s>>>(lv, n, u, bs, uo, dw32, partials);
   k_final_sum<<<1, 1024, 0, s>>>(partials, kNormBlocks, out);
   count_launches(2);
   return cudaGetLastError();
@@ -809,7 +818,8 @@ cudaError_t launch_sens_final(int N, int chunks, const double* chi, Simp6 sp, co
 
 #define STMG_INST(T)                                                                                              \
   template cudaError_t launch_sweep<T>(const LevelView<T>&, bool, const T*, const T*, T*, cudaStream_t);          \
-  template cudaError_t launch_sweep_norm<T>(const LevelView<T>&, bool, const T*, const T*, T*, double*, double*,  \
+  template cudaError_t launch_sweep_norm<T>(const LevelView<T>&, bool, const T*, const T*, T*, const float*,     \
+                                            double*, double*,                                                   \
                                             cudaStream_t);                                                        \
   template cudaError_t launch_residual<T>(const LevelView<T>&, bool, const T*, const T*, T*, cudaStream_t);       \
   template cudaError_t launch_apply<T>(const LevelView<T>&, bool, const T*, T*, cudaStream_t);                    \
