@@ -47,6 +47,7 @@ def parse():
     p.add_argument("--no-variant", action="store_true", help="skip the other-precision solve of the same workload")
     p.add_argument("--mixed-inner", type=int, default=3, help="FP32 V-cycles per FP64 defect in the mixed scheme")
     p.add_argument("--mixed-first", type=int, default=3, help="FP32 V-cycles on the first defect in the mixed scheme")
+    p.add_argument("--max-coarse-dofs", type=int, default=0, help="planner: stop at a level this small (0: default)")
     p.add_argument("--serving-requests", type=int, default=64,
                    help="requests of the 512-request serving trace to replay (0: skip serving)")
     p.add_argument("--serving-workers", type=int, default=6)
@@ -244,9 +245,13 @@ def precision_opts(args, precision):
     return {"mixed_inner_cycles": args.mixed_inner, "mixed_first_cycles": args.mixed_first}
 
 
-def workload_opts(w):
-    """Solver options the workload fixes (nu = 20 for the rough differentiation field)."""
-    return {"nu": w["nu"]} if "nu" in w else {}
+def workload_opts(w, args=None):
+    """Solver options the workload fixes (nu = 20 for the rough differentiation field), and
+    the planner's coarsest-level size when given on the command line."""
+    o = {"nu": w["nu"]} if "nu" in w else {}
+    if args is not None and args.max_coarse_dofs > 0:
+        o["max_coarse_dofs"] = args.max_coarse_dofs
+    return o
 
 
 SERVING_OPTS = dict(precision="mixed", tol=TOL, nu=60, max_cycles=300)
@@ -327,7 +332,7 @@ def main():
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     solver = pkg.Solver(N, NT, L, tT, k, c, precision=args.precision, tol=TOL, **precision_opts(args, args.precision),
-                        **workload_opts(w))
+                        **workload_opts(w, args))
     setup_ms = 1e3 * (time.perf_counter() - t0)
     levels, path = solver.num_levels, solver.path()
 
@@ -434,7 +439,7 @@ def main():
     variant = None
     if not args.no_variant:
         other = "mixed" if args.precision == "fp64" else "fp64"
-        s2 = pkg.Solver(N, NT, L, tT, k, c, precision=other, tol=TOL, **precision_opts(args, other), **workload_opts(w))
+        s2 = pkg.Solver(N, NT, L, tT, k, c, precision=other, tol=TOL, **precision_opts(args, other), **workload_opts(w, args))
         for _ in range(max(1, args.warmup)):
             s2.solve(u, q=q)
         torch.cuda.synchronize()
@@ -472,7 +477,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
             "data": "synthetic",
-            "config": {"workload": w["name"], "N": N, "NT": NT, "dofs": dofs, "precision": args.precision, **precision_opts(args, args.precision), **workload_opts(w),
+            "config": {"workload": w["name"], "N": N, "NT": NT, "dofs": dofs, "precision": args.precision, **precision_opts(args, args.precision), **workload_opts(w, args),
                        "tol": TOL, "levels": levels, "path": path, "cycles": cycles,
                        "relres": relres, "converged": ok, "setup_ms": setup_ms,
                        "l2": "no flush: every vector (%d MB) exceeds the 129 MB L2" % (dofs * 8 // 2 ** 20),
