@@ -78,7 +78,10 @@ typedef struct {
     double deff_fixed;         /* [0] > 0: design-independent D_eff on every level (Sec. 7.2) */
     int precision;             /* [STMG_FP64] STMG_FP64: FP64 V-cycles (Alg. 1 as written).
                                   STMG_MIXED: FP64 defect correction around FP32 V-cycles; the fine
-                                  residual, the coarse material and the coarsest solve stay FP64. */
+                                  residual, the coarse material and the coarsest solve stay FP64.
+                                  Both: the FP32 parts (the cycles, the termination norms) run on
+                                  copies scaled by a power of two chosen from ||b||, so the solution
+                                  of J u = 2^m b is exactly 2^m u for any b whose squares fit FP64. */
     double tol;                /* [1e-10] stop when ||J u - b|| / ||b|| < tol (Sec. 3.1) */
     double div_tol;            /* [1e9] stop (diverged) when the relative residual exceeds this */
     int max_cycles;            /* [100] cycle limit (Sec. 3.1) */

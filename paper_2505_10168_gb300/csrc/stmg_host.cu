@@ -519,6 +519,8 @@ std::vector<int> sweep_passes(int nu) {
   return p;
 }
 
+int* kexp(stmg_t h);
+
 StreamArgs stream_args(const Level& L, double omega) {
   StreamArgs a{};
   a.N = L.N;
@@ -540,7 +542,7 @@ stmg_status vcycle32_fused(stmg_t h, int l, bool adj, double* u64, bool zero_sta
   Level& L = h->lev[l];
   if (l == (int)h->lev.size() - 1) {
     CK(exact_level<float>(h, L, adj, L.b32, L.u32));
-    if (u64) CK(launch_add_correction(L.nvec, u64, L.u32, h->s));
+    if (u64) CK(launch_add_correction(L.nvec, u64, L.u32, kexp(h), h->s));
     return STMG_OK;
   }
   Level& C = h->lev[l + 1];
@@ -578,6 +580,7 @@ stmg_status vcycle32_fused(stmg_t h, int l, bool adj, double* u64, bool zero_sta
     const bool last = p + 1 == passes.size();
     a.u_out = (last && u64) ? nullptr : out;
     a.u64 = (last && u64) ? u64 : nullptr;
+    a.kexp = kexp(h);
     int mode = kStreamPlain;
     if (p == 0) {
       mode = xc ? kStreamUpX : (h->o.interp == STMG_INTERP_BILINEAR ? kStreamUpTB : kStreamUpT);
@@ -645,9 +648,15 @@ stmg_status assemble_into(stmg_t h, const double* q, double* b) {
 }
 
 // ||b - J u||^2 on level 0 in FP64 (u null: ||b||^2).
-stmg_status resnorm2(stmg_t h, bool adj, const double* u, const double* b, double* out) {
+// The device int holding the scale exponent k of the finest level's FP32 arithmetic (see
+// scale_exp): the last of the handle's device scalars.
+int* kexp(stmg_t h) { return reinterpret_cast<int*>(h->scal + 7); }
+
+// ||b - J u||^2 on level 0; set_scale: u is null and k is chosen from ||b||.
+stmg_status resnorm2(stmg_t h, bool adj, const double* u, const double* b, double* out, bool set_scale = false) {
   Level& L = h->lev[0];
-  CK(launch_resnorm<double>(view<double>(L, h->o.omega), adj, u, b, h->partials, h->scal, h->s));
+  CK(launch_resnorm<double>(view<double>(L, h->o.omega), adj, u, b, h->partials, h->scal, h->s,
+                            set_scale ? kexp(h) : nullptr));
   return read_scalar(h, h->scal, out);
 }
 
@@ -715,7 +724,7 @@ stmg_status solve_loop(stmg_t h, bool adj, bool warm, int* cycles_out, double* r
   const LevelView<double> lv = view<double>(L, o.omega);
   if (!warm) CK(cudaMemsetAsync(L.u, 0, L.nvec * sizeof(double), h->s));
   double nb2 = 0.0;
-  CKS(resnorm2(h, adj, nullptr, L.b, &nb2));
+  CKS(resnorm2(h, adj, nullptr, L.b, &nb2, true));
   int cycles = 0;
   double rel = 0.0;
   stmg_status st = STMG_EMAXITER;
@@ -727,8 +736,12 @@ stmg_status solve_loop(stmg_t h, bool adj, bool warm, int* cycles_out, double* r
   } else if (o.precision == STMG_MIXED) {
     const double nb = std::sqrt(nb2);
     double r2 = nb2;
-    CK(launch_defect(lv, L.cf32, adj, L.u, L.b, L.b32, h->partials, h->scal, h->s));
-    CKS(read_scalar(h, h->scal, &r2));
+    if (warm) {
+      CK(launch_defect(lv, L.cf32, adj, L.u, L.b, kexp(h), L.b32, h->partials, h->scal, h->s));
+      CKS(read_scalar(h, h->scal, &r2));
+    } else {
+      CK(launch_rhs32(lv, L.b, kexp(h), L.b32, h->s));  // u = 0: the defect is b itself
+    }
     rel = std::sqrt(r2) / nb;
     if (rel < o.tol) st = STMG_OK;
     // the first defect is solved by several FP32 cycles (an inner iteration far above the
@@ -736,7 +749,7 @@ stmg_status solve_loop(stmg_t h, bool adj, bool warm, int* cycles_out, double* r
     const int first = std::max(1, o.mixed_first_cycles);
     if (st != STMG_OK && first > 1 && o.nu > 0 && o.max_cycles >= first) {
       for (int j = 1; j <= first; ++j) CKS(vcycle32_fused(h, 0, adj, j == first ? L.u : nullptr, j == 1));
-      CK(launch_defect(lv, L.cf32, adj, L.u, L.b, L.b32, h->partials, h->scal, h->s));
+      CK(launch_defect(lv, L.cf32, adj, L.u, L.b, kexp(h), L.b32, h->partials, h->scal, h->s));
       CKS(read_scalar(h, h->scal, &r2));
       rel = std::sqrt(r2) / nb;
       cycles = first;
@@ -755,9 +768,9 @@ stmg_status solve_loop(stmg_t h, bool adj, bool warm, int* cycles_out, double* r
             for (int j = 1; j <= inner; ++j) CKS(vcycle32_fused(h, 0, adj, j == inner ? L.u : nullptr, j == 1));
           } else {
             CKS(vcycle<float>(h, 0, adj, true, false));
-            CK(launch_add_correction(L.nvec, L.u, L.u32, h->s));
+            CK(launch_add_correction(L.nvec, L.u, L.u32, kexp(h), h->s));
           }
-          CK(launch_defect(lv, L.cf32, adj, L.u, L.b, L.b32, h->partials, h->scal, h->s));
+          CK(launch_defect(lv, L.cf32, adj, L.u, L.b, kexp(h), L.b32, h->partials, h->scal, h->s));
           return STMG_OK;
         }));
       }
@@ -779,7 +792,8 @@ stmg_status solve_loop(stmg_t h, bool adj, bool warm, int* cycles_out, double* r
     // the first sweep of cycle 1 (with the norm of the starting iterate if it is not 0)
     if (!one_level && o.nu > 0) {
       if (warm) {
-        CK(launch_sweep_norm<double>(lv, adj, L.u, L.b, L.t, L.cf32 + (size_t)kDW * L.pitch, h->partials, h->scal, h->s));
+        CK(launch_sweep_norm<double>(lv, adj, L.u, L.b, L.t, L.cf32 + (size_t)kDW * L.pitch, kexp(h), h->partials,
+                                            h->scal, h->s));
         CKS(read_scalar(h, h->scal, &r2));
       } else {
         CK(cudaMemcpyAsync(L.t, L.b, L.nvec * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
@@ -801,7 +815,8 @@ stmg_status solve_loop(stmg_t h, bool adj, bool warm, int* cycles_out, double* r
           CKS(capture_graph(h, &gx, &gk, [&]() -> stmg_status {
             std::swap(L.u, L.t);
             CKS(vcycle<double>(h, 0, adj, false, true));
-            CK(launch_sweep_norm<double>(lv, adj, L.u, L.b, L.t, L.cf32 + (size_t)kDW * L.pitch, h->partials, h->scal, h->s));
+            CK(launch_sweep_norm<double>(lv, adj, L.u, L.b, L.t, L.cf32 + (size_t)kDW * L.pitch, kexp(h), h->partials,
+                                            h->scal, h->s));
             return STMG_OK;
           }));
           if (L.u != u_before) return fail(h, STMG_ECUDA, "internal: odd number of level-0 swaps in a cycle");
@@ -1062,6 +1077,8 @@ static stmg_status create_common(stmg_t* out, int nel, int nt, double L, double 
   if (st == STMG_OK) st = read_material(h, nel, k_el, c_el, hk, hc);
   if (st == STMG_OK) st = dalloc(h, &h->partials, kNormBlocks);
   if (st == STMG_OK) st = dalloc(h, &h->scal, 8);
+  if (st == STMG_OK && cudaMemset(h->scal, 0, 8 * sizeof(double)) != cudaSuccess)
+    st = fail(h, STMG_ECUDA, "cudaMemset of the device scalars failed");
   if (st == STMG_OK) {
     cudaError_t e = cudaStreamCreateWithFlags(&h->cs, cudaStreamNonBlocking);
     if (e != cudaSuccess) st = fail(h, STMG_ECUDA, "cudaStreamCreateWithFlags: %s", cudaGetErrorString(e));
@@ -1459,12 +1476,14 @@ stmg_status stmg_vcycle(stmg_t h, int adjoint, double* u, const double* b) {
   CKS(copy_in(h, L.b, L.pitch, b, L.NT + 1, L.N + 1));
   CK(launch_scale<double>(view<double>(L, h->o.omega), true, L.b, h->s));
   if (h->o.precision == STMG_MIXED) {
-    CK(launch_defect(view<double>(L, h->o.omega), L.cf32, adjoint != 0, L.u, L.b, L.b32, h->partials, h->scal, h->s));
+    CK(cudaMemsetAsync(kexp(h), 0, sizeof(int), h->s));  // one cycle: FP32 arithmetic unscaled
+    CK(launch_defect(view<double>(L, h->o.omega), L.cf32, adjoint != 0, L.u, L.b, kexp(h), L.b32, h->partials,
+                     h->scal, h->s));
     if (h->o.nu > 0) {
       CKS(vcycle32_fused(h, 0, adjoint != 0, L.u));
     } else {
       CKS(vcycle<float>(h, 0, adjoint != 0, true, false));
-      CK(launch_add_correction(L.nvec, L.u, L.u32, h->s));
+      CK(launch_add_correction(L.nvec, L.u, L.u32, kexp(h), h->s));
     }
   } else {
     CKS(vcycle<double>(h, 0, adjoint != 0, false, false));

@@ -90,27 +90,39 @@ struct ThomasView {
 };
 
 // FP64 <-> FP32 conversions by IEEE-754 bit fields on the integer pipe (on this GPU the
-// conversion instructions share the slow FP64 pipe).  Magnitudes below 2^-126 become
-// signed zero; the mixed scheme's values are far from both ends of the FP32 range.
-// to_f32_trunc truncates the mantissa (relative error < 2^-23); to_f64 is exact.
-__device__ __forceinline__ float to_f32_trunc(double d) {
+// conversion instructions share the slow FP64 pipe), with an exact power-of-two scale:
+// to_f32_trunc(d, k) = d 2^k with the mantissa truncated (relative error < 2^-23), signed
+// zero below 2^-126 and infinity above the FP32 range; to_f64(f, k) = f 2^k exactly (FP32
+// subnormals, which the FP32 kernels flush, become zero).  |k| <= kMaxScaleExp.
+constexpr int kMaxScaleExp = 800;
+__device__ __forceinline__ float to_f32_trunc(double d, int k = 0) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(d);
   const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
   const unsigned sign = hi & 0x80000000u;
-  const int e = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
+  const int be = (int)((hi >> 20) & 0x7ffu);
+  const int e = be - 1023 + 127 + k;
   const unsigned mant = ((hi & 0xfffffu) << 3) | (lo >> 29);
   unsigned r = sign | ((unsigned)e << 23) | mant;
-  r = e <= 0 ? sign : r;
+  r = (e <= 0 || be == 0) ? sign : r;
   r = e >= 255 ? (sign | 0x7f800000u) : r;
   return __uint_as_float(r);
 }
-__device__ __forceinline__ double to_f64(float f) {
+__device__ __forceinline__ double to_f64(float f, int k = 0) {
   const unsigned b = __float_as_uint(f);
   const unsigned sign = b & 0x80000000u, e = (b >> 23) & 0xffu, m = b & 0x7fffffu;
-  const unsigned hi = e == 0 ? sign : (sign | ((e + 1023u - 127u) << 20) | (m >> 3));
+  const unsigned hi = e == 0 ? sign : (sign | ((unsigned)((int)e + 1023 - 127 + k) << 20) | (m >> 3));
   const unsigned lo = e == 0 ? 0u : (m << 29);
   return __hiloint2double((int)hi, (int)lo);
 }
+
+// The power-of-two scale 2^k of the FP32 arithmetic on the finest level (kept in device
+// memory so that captured graphs read the current one): the FP32 copies of FP64 residuals
+// are scaled by 2^k, FP32 corrections are scaled back by 2^-k, and the FP32 termination
+// norms are taken of 2^k r and scaled back by 2^-2k.  k is chosen when ||b|| is summed,
+// so that 2^k b has an RMS in [1, 4): magnitudes of b far outside the FP32 range neither
+// flush to zero nor overflow.  In range, the result is independent of k (a power-of-two
+// scale commutes with every rounding).
+__device__ __forceinline__ int scale_exp(const int* kexp) { return kexp ? *kexp : 0; }
 
 // Programmatic dependent launch (sm_90 and later): a kernel launched with launch_pdl may
 // start while the previous kernel of its stream drains; it calls pdl_wait() before its first
@@ -152,7 +164,7 @@ cudaError_t launch_sweep(const LevelView<T>& lv, bool adj, const T* u, const T* 
 // FP32 D / omega (the norm is accumulated in FP32 per thread).
 template <typename T>
 cudaError_t launch_sweep_norm(const LevelView<T>& lv, bool adj, const T* u, const T* bs, T* uo, const float* dw32,
-                              double* partials, double* out, cudaStream_t s);
+                              const int* kexp, double* partials, double* out, cudaStream_t s);
 // r = b - J u from the stored b'.
 template <typename T>
 cudaError_t launch_residual(const LevelView<T>& lv, bool adj, const T* u, const T* bs, T* r, cudaStream_t s);
@@ -179,17 +191,23 @@ cudaError_t launch_exact_scan(const ThomasView& tv, bool adj, int K, const doubl
 template <typename T>
 cudaError_t launch_scale(const LevelView<T>& lv, bool to_scaled, T* x, cudaStream_t s);
 
-// ||b - J u||^2 (u == nullptr: ||b||^2) from the stored b' into out[0].
+// ||b - J u||^2 (u == nullptr: ||b||^2) from the stored b' into out[0]; with kset, also the
+// scale exponent of the FP32 arithmetic from this norm (see scale_exp).
 template <typename T>
 cudaError_t launch_resnorm(const LevelView<T>& lv, bool adj, const T* u, const T* bs, double* partials, double* out,
-                           cudaStream_t s);
-// Mixed scheme, FP64 level 0: y = (omega/D)(b - J u) stored as FP32 (it is the scaled
-// right-hand side of the FP32 cycle), with ||b - J u||^2 (accumulated in FP32 per thread;
-// it only feeds the termination test) into out[0].  coef32: the level's FP32 coefficients.
+                           cudaStream_t s, int* kset = nullptr);
+// Mixed scheme, FP64 level 0: y = (omega/D)(b - J u) stored as FP32 scaled by 2^k (it is the
+// scaled right-hand side of the FP32 cycle), with ||b - J u||^2 (of 2^k r accumulated in
+// FP32 per thread, scaled back; it only feeds the termination test) into out[0].
+// coef32: the level's FP32 coefficients.
 cudaError_t launch_defect(const LevelView<double>& lv, const float* coef32, bool adj, const double* u,
-                          const double* bs, float* ys32, double* partials, double* out, cudaStream_t s);
-// u64 += double(e32) over the whole padded array.
-cudaError_t launch_add_correction(size_t n, double* u, const float* e, cudaStream_t s);
+                          const double* bs, const int* kexp, float* ys32, double* partials, double* out,
+                          cudaStream_t s);
+// The same for u = 0: ys32 = b' 2^k (truncated to FP32) over the level's DOFs.
+cudaError_t launch_rhs32(const LevelView<double>& lv, const double* bs, const int* kexp, float* ys32,
+                         cudaStream_t s);
+// u64 += double(e32) 2^-k over the whole padded array (kexp null: k = 0).
+cudaError_t launch_add_correction(size_t n, double* u, const float* e, const int* kexp, cudaStream_t s);
 // a . b over the padded arrays (padding is zero) into out[0]; deterministic.
 cudaError_t launch_dot(size_t n, const double* a, const double* b, double* partials, double* out, cudaStream_t s);
 

@@ -114,16 +114,19 @@ __device__ __forceinline__ double block_sum(double v) {
 
 // Sweep that also accumulates ||b - J u||^2 of the input iterate (fixed grid, grid-stride).
 // The sweep's increment y = uo - u is the scaled residual (omega / D)(b - J u), exact in T;
-// the norm only decides termination, so r = (D / omega) y is formed and squared in FP32 per
-// thread (y truncated by its bit fields, dw32 = the FP32 copy of D / omega) and summed in
-// FP64 across the block: in FP64 the kernel costs 7 operations per DOF, a plain sweep 6.
+// the norm only decides termination, so 2^k r = (D / omega) 2^k y is formed and squared in
+// FP32 per thread (y scaled and truncated by its bit fields, dw32 = the FP32 copy of
+// D / omega; 2^k from scale_exp, undone in the final sum) and summed in FP64 across the
+// block: in FP64 the kernel costs 7 operations per DOF, a plain sweep 6.
 template <typename T, bool ADJ>
 __global__ void __launch_bounds__(kThreads) k_sweep_norm(LevelView<T> lv, uint32_t total, const T* __restrict__ u,
                                                          const T* __restrict__ bs, T* __restrict__ uo,
                                                          const float* __restrict__ dw32,
+                                                         const int* __restrict__ kexp,
                                                          double* __restrict__ partials) {
   float acc = 0.f;
   const float Wo32 = (float)lv.Wo;
+  const int k = scale_exp(kexp);
   for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
     int n, i;
     split_index(idx, lv.fd, n, i);
@@ -131,7 +134,7 @@ __global__ void __launch_bounds__(kThreads) k_sweep_norm(LevelView<T> lv, uint32
     const T y = scaled_residual<T, ADJ>(lv, u, bs, n, i, p);
     uo[p] = u[p] + y;
     float yf;
-    if constexpr (std::is_same<T, double>::value) yf = to_f32_trunc(y);
+    if constexpr (std::is_same<T, double>::value) yf = to_f32_trunc(y, k);
     else yf = y;
     const float r = ((n == 0 || i == 0) ? Wo32 : dw32[i]) * yf;
     acc = fmaf(r, r, acc);
@@ -467,34 +470,54 @@ __global__ void __launch_bounds__(kThreads) k_resnorm(LevelView<T> lv, uint32_t 
 }
 
 // Mixed-scheme defect on the finest level: y = (omega/D)(b - J u) in FP64 (the scaled
-// residual of the FP64 iterate), stored as FP32 as the right-hand side of the next FP32
-// cycle.  The squared norm, which only feeds the termination test, is accumulated in FP32
-// per thread (r = (D/omega) y with the FP32 coefficients) and summed in FP64 across the
-// block: 6 FP64 FMAs per DOF (the conversion to FP32 runs on the integer pipe).
-template <bool ADJ>
+// residual of the FP64 iterate), stored as FP32 scaled by 2^k as the right-hand side of the
+// next FP32 cycle.  The squared norm, which only feeds the termination test, is accumulated
+// in FP32 per thread (2^k r = (D/omega) 2^k y with the FP32 coefficients) and summed in FP64
+// across the block: 6 FP64 FMAs per DOF (the conversion to FP32 runs on the integer pipe).
+// ZERO: u = 0, so y = b' (no FP64 arithmetic; the norm is not formed).
+template <bool ADJ, bool ZERO>
 __global__ void __launch_bounds__(kThreads) k_defect(LevelView<double> lv, uint32_t total, const float* __restrict__ dw32,
                                                      const double* __restrict__ u, const double* __restrict__ bs,
-                                                     float* __restrict__ ys32, double* __restrict__ partials) {
+                                                     const int* __restrict__ kexp, float* __restrict__ ys32,
+                                                     double* __restrict__ partials) {
   float acc = 0.f;
   const float Wo32 = (float)lv.Wo;
+  const int k = scale_exp(kexp);
   for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
     int n, i;
     split_index(idx, lv.fd, n, i);
     const size_t p = (size_t)n * lv.pitch + i;
-    const float y = to_f32_trunc(scaled_residual<double, ADJ>(lv, u, bs, n, i, p));
+    if (ZERO) {
+      ys32[p] = to_f32_trunc(bs[p], k);
+      continue;
+    }
+    const float y = to_f32_trunc(scaled_residual<double, ADJ>(lv, u, bs, n, i, p), k);
     ys32[p] = y;
     const float r = ((n == 0 || i == 0) ? Wo32 : dw32[i]) * y;
     acc = fmaf(r, r, acc);
   }
+  if (ZERO) return;
   const double s = block_sum<kThreads>((double)acc);
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
-__global__ void k_final_sum(const double* __restrict__ partials, int n, double* __restrict__ out) {
+// Sum of the per-block partials into out[0].  kget: the partials are of 2^k r (k from
+// scale_exp), so the sum is scaled by 2^-2k.  kset: the partials are ||b||^2 over `count`
+// DOFs; sets k so that 2^k b has an RMS in [1, 2) (k = 0 for a zero or non-finite sum).
+__global__ void k_final_sum(const double* __restrict__ partials, int n, double* __restrict__ out,
+                            const int* __restrict__ kget, int* __restrict__ kset, double count) {
   double acc = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) acc += partials[i];
   const double s = block_sum<1024>(acc);
-  if (threadIdx.x == 0) out[0] = s;
+  if (threadIdx.x == 0) {
+    out[0] = kget ? ldexp(s, -2 * *kget) : s;
+    if (kset) {
+      const double ms = s / count;
+      int k = 0;
+      if (ms > 0.0 && isfinite(ms)) k = -(ilogb(ms) >> 1);
+      kset[0] = max(-kMaxScaleExp, min(kMaxScaleExp, k));
+    }
+  }
 }
 
 __global__ void __launch_bounds__(kThreads) k_dot(size_t n, const double* __restrict__ a,
@@ -507,9 +530,10 @@ __global__ void __launch_bounds__(kThreads) k_dot(size_t n, const double* __rest
 }
 
 __global__ void __launch_bounds__(kThreads) k_add_correction(size_t n, double* __restrict__ u,
-                                                             const float* __restrict__ e) {
+                                                             const float* __restrict__ e,
+                                                             const int* __restrict__ kexp) {
   const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  if (i < n) u[i] += (double)e[i];
+  if (i < n) u[i] += to_f64(e[i], -scale_exp(kexp));
 }
 
 // Stencil coefficients per node from element k, c (Sec. 2.2 element matrices, Appendix A).
@@ -653,11 +677,12 @@ cudaError_t launch_sweep(const LevelView<T>& lv, bool adj, const T* u, const T* 
 
 template <typename T>
 cudaError_t launch_sweep_norm(const LevelView<T>& lv, bool adj, const T* u, const T* bs, T* uo, const float* dw32,
-                              double* partials, double* out, cudaStream_t s) {
+                              const int* kexp, double* partials, double* out, cudaStream_t s) {
   const uint32_t n = dofs(lv);
-  if (adj) k_sweep_norm<T, true><<<kNormBlocks, kThreads, 0, s>>>(lv, n, u, bs, uo, dw32, partials);
-  else k_sweep_norm<T, false><<<kNormBlocks, kThreads, 0, s>>>(lv, n, u, bs, uo, dw32, partials);
-  k_final_sum<<<1, 1024, 0, s>>>(partials, kNormBlocks, out);
+  if (!std::is_same<T, double>::value) kexp = nullptr;  // FP32 levels are not rescaled
+  if (adj) k_sweep_norm<T, true><<<kNormBlocks, kThreads, 0, s>>>(lv, n, u, bs, uo, dw32, kexp, partials);
+  else k_sweep_norm<T, false><<<kNormBlocks, kThreads, 0, s>>>(lv, n, u, bs, uo, dw32, kexp, partials);
+  k_final_sum<<<1, 1024, 0, s>>>(partials, kNormBlocks, out, kexp, nullptr, 0.0);
   count_launches(2);
   return cudaGetLastError();
 }
@@ -746,35 +771,43 @@ cudaError_t launch_scale(const LevelView<T>& lv, bool to_scaled, T* x, cudaStrea
 
 template <typename T>
 cudaError_t launch_resnorm(const LevelView<T>& lv, bool adj, const T* u, const T* bs, double* partials, double* out,
-                           cudaStream_t s) {
+                           cudaStream_t s, int* kset) {
   const uint32_t n = dofs(lv);
   if (adj) k_resnorm<T, T, true><<<kNormBlocks, kThreads, 0, s>>>(lv, n, u, bs, (T*)nullptr, partials);
   else k_resnorm<T, T, false><<<kNormBlocks, kThreads, 0, s>>>(lv, n, u, bs, (T*)nullptr, partials);
-  k_final_sum<<<1, 1024, 0, s>>>(partials, kNormBlocks, out);
+  k_final_sum<<<1, 1024, 0, s>>>(partials, kNormBlocks, out, nullptr, kset, (double)n);
   count_launches(2);
   return cudaGetLastError();
 }
 
 cudaError_t launch_defect(const LevelView<double>& lv, const float* coef32, bool adj, const double* u,
-                          const double* bs, float* ys32, double* partials, double* out, cudaStream_t s) {
+                          const double* bs, const int* kexp, float* ys32, double* partials, double* out,
+                          cudaStream_t s) {
   const uint32_t n = dofs(lv);
   const float* dw32 = coef32 + (size_t)kDW * lv.pitch;
-  if (adj) k_defect<true><<<kNormBlocks, kThreads, 0, s>>>(lv, n, dw32, u, bs, ys32, partials);
-  else k_defect<false><<<kNormBlocks, kThreads, 0, s>>>(lv, n, dw32, u, bs, ys32, partials);
-  k_final_sum<<<1, 1024, 0, s>>>(partials, kNormBlocks, out);
+  if (adj) k_defect<true, false><<<kNormBlocks, kThreads, 0, s>>>(lv, n, dw32, u, bs, kexp, ys32, partials);
+  else k_defect<false, false><<<kNormBlocks, kThreads, 0, s>>>(lv, n, dw32, u, bs, kexp, ys32, partials);
+  k_final_sum<<<1, 1024, 0, s>>>(partials, kNormBlocks, out, kexp, nullptr, 0.0);
   count_launches(2);
   return cudaGetLastError();
 }
 
-cudaError_t launch_add_correction(size_t n, double* u, const float* e, cudaStream_t s) {
-  k_add_correction<<<blocks_for((long long)n), kThreads, 0, s>>>(n, u, e);
+cudaError_t launch_rhs32(const LevelView<double>& lv, const double* bs, const int* kexp, float* ys32,
+                         cudaStream_t s) {
+  k_defect<false, true><<<kNormBlocks, kThreads, 0, s>>>(lv, dofs(lv), nullptr, nullptr, bs, kexp, ys32, nullptr);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_add_correction(size_t n, double* u, const float* e, const int* kexp, cudaStream_t s) {
+  k_add_correction<<<blocks_for((long long)n), kThreads, 0, s>>>(n, u, e, kexp);
   count_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_dot(size_t n, const double* a, const double* b, double* partials, double* out, cudaStream_t s) {
   k_dot<<<kNormBlocks, kThreads, 0, s>>>(n, a, b, partials);
-  k_final_sum<<<1, 1024, 0, s>>>(partials, kNormBlocks, out);
+  k_final_sum<<<1, 1024, 0, s>>>(partials, kNormBlocks, out, nullptr, nullptr, 0.0);
   count_launches(2);
   return cudaGetLastError();
 }
@@ -819,7 +852,7 @@ cudaError_t launch_sens_final(int N, int chunks, const double* chi, Simp6 sp, co
 #define STMG_INST(T)                                                                                              \
   template cudaError_t launch_sweep<T>(const LevelView<T>&, bool, const T*, const T*, T*, cudaStream_t);          \
   template cudaError_t launch_sweep_norm<T>(const LevelView<T>&, bool, const T*, const T*, T*, const float*,     \
-                                            double*, double*,                                                   \
+                                            const int*, double*, double*,                                       \
                                             cudaStream_t);                                                        \
   template cudaError_t launch_residual<T>(const LevelView<T>&, bool, const T*, const T*, T*, cudaStream_t);       \
   template cudaError_t launch_apply<T>(const LevelView<T>&, bool, const T*, T*, cudaStream_t);                    \
@@ -829,7 +862,7 @@ cudaError_t launch_sens_final(int N, int chunks, const double* chi, Simp6 sp, co
   template cudaError_t launch_exact_scan<T>(const ThomasView&, bool, int, const double*, const T*, T*, cudaStream_t); \
   template cudaError_t launch_scale<T>(const LevelView<T>&, bool, T*, cudaStream_t);                              \
   template cudaError_t launch_resnorm<T>(const LevelView<T>&, bool, const T*, const T*, double*, double*,         \
-                                         cudaStream_t);
+                                         cudaStream_t, int*);
 STMG_INST(double)
 STMG_INST(float)
 #undef STMG_INST

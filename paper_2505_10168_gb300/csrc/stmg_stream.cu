@@ -299,6 +299,7 @@ __global__ void __launch_bounds__(Width<MODE>::kThreads, Width<MODE>::kMinBlocks
   };
 
   // One row: consume its ring slot, sweep, store, restrict.
+  int ku = 0;  // exponent of the scale of the FP64 accumulate (set after pdl_wait)
   auto row = [&](auto dir_tag, const int j, const Pipe<S, kVec>& in, Pipe<S, kVec>& out) {
     constexpr bool DIR = decltype(dir_tag)::value;
     const int n = first + j * step;
@@ -346,8 +347,8 @@ __global__ void __launch_bounds__(Width<MODE>::kThreads, Width<MODE>::kMinBlocks
 #pragma unroll
       for (int q = 0; q < kVec / 2; ++q) {
         acc[q] = *reinterpret_cast<const double2*>(slot + (R::k64 + q) * 32 + lane);
-        acc[q].x += to_f64(out.v[S].e[2 * q]);
-        acc[q].y += to_f64(out.v[S].e[2 * q + 1]);
+        acc[q].x += to_f64(out.v[S].e[2 * q], ku);
+        acc[q].y += to_f64(out.v[S].e[2 * q + 1], ku);
       }
       if (emit && owner) {
         double2* dst = reinterpret_cast<double2*>(a.u64 + (size_t)n * P + col);
@@ -424,6 +425,7 @@ __global__ void __launch_bounds__(Width<MODE>::kThreads, Width<MODE>::kMinBlocks
   // built.  The rows come from the kernels before this one: wait for them (a no-op unless
   // this grid was launched ahead of its predecessor's end) and let the next pass launch.
   pdl_wait();
+  if (!DOWN && a.u64 != nullptr) ku = -scale_exp(a.kexp);
 #pragma unroll
   for (int j = 0; j < kD; ++j) fetch(j);
   int j = 0;

@@ -22,7 +22,8 @@ struct StreamArgs {
   const float* u_in;       // starting iterate (ignored when zero_init)
   const float* bs;         // scaled right-hand side b'
   float* u_out;            // result, or nullptr when u64 is set
-  double* u64;             // finest level of the mixed scheme: u64 += result
+  double* u64;             // finest level of the mixed scheme: u64 += result 2^-k
+  const int* kexp;         // k (see scale_exp), read with u64
   int zero_init;           // the starting iterate is 0
   // coarse level: restriction target (DOWN) or correction source (UP)
   int pc;                  // coarse pitch
