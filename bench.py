@@ -257,6 +257,53 @@ def workload_opts(w, args=None):
 SERVING_OPTS = dict(precision="mixed", tol=TOL, nu=60, max_cycles=300)
 
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture
+# of the kernel on the named workload; a kernel changed since its capture has no entry.
+NCU_TRAFFIC = {
+    ("config2", "k_sweep<double>"): 1.590e9,
+    ("config2", "k_defect (FP64, finest level)"): 1.3329e9,
+    ("config2", "k_stream UP + FP64 accumulate (finest level)"): 1.7467e9,
+    ("config2", "k_stream DOWN from zero (finest level)"): 0.6300e9,
+}
+
+
+def mixed_rooflines(solver, stream, wname, dofs, nu, reps=20):
+    """The mixed scheme's three heaviest steps, each launched alone `reps` times on the
+    solver's stream (after its timed solves) and timed with CUDA events there: the FP64
+    defect (6 FP64 FMA, 20 B per DOF), the finest level's UP pass that adds into the FP64
+    iterate (26 B per DOF) and its DOWN pass from zero (10 B per DOF).  Shares of the solve
+    come from the launch list, not from here."""
+    import torch
+
+    if nu > 5:
+        return [{"skipped": "nu > 5: each half of a level is several passes"}]
+    hbm = measured_peaks().get("hbm_gbs", 6788.3)
+    out = []
+    for kind, name, nbytes, flops in (("defect", "k_defect (FP64, finest level)", 20.0, 12.0),
+                                      ("up", "k_stream UP + FP64 accumulate (finest level)", 26.0, None),
+                                      ("down", "k_stream DOWN from zero (finest level)", 10.0, None)):
+        solver.mixed_pass(0, kind)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            solver.mixed_pass(0, kind)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        gbs = nbytes * dofs / (ms * 1e-3) / 1e9
+        if flops is None:
+            r = {"kernel": name, "bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm}
+        else:
+            tf = flops * dofs / (ms * 1e-3) / 1e12
+            r = {"kernel": name, "bound": "alu", "achieved": tf, "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
+                 "frac": tf / NOMINAL_FP64_TFLOPS, "hbm_gbs": gbs, "hbm_frac_of_measured": gbs / hbm}
+        r.update({"traffic": NCU_TRAFFIC.get((wname, name)), "ms_per_launch": ms, "algorithmic_bytes_per_dof": nbytes,
+                  "peak_source": "measured HBM copy" if flops is None else "nominal GB300 FP64"})
+        out.append(r)
+    return out
+
+
 def run_serving(nreq, workers, inner=3, compare=8):
     """Closed loop (all requests queued at once) for throughput, then the same requests
     with their Poisson gaps rescaled to 0.5x, 0.8x and 1.0x that throughput for latency
@@ -387,7 +434,7 @@ def main():
         ach = flops / (sweep_ms * 1e-3) / 1e12
         roofline = {"kernel": "k_sweep<double> (finest level)", "bound": "alu", "achieved": ach,
                     "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s", "frac": ach / NOMINAL_FP64_TFLOPS,
-                    "traffic": None, "ms_per_launch": sweep_ms,
+                    "traffic": NCU_TRAFFIC.get((w["name"], "k_sweep<double>")), "ms_per_launch": sweep_ms,
                     "hbm_gbs": bytes_alg / (sweep_ms * 1e-3) / 1e9,
                     "hbm_frac_of_measured": bytes_alg / (sweep_ms * 1e-3) / 1e9 /
                     measured_peaks().get("hbm_gbs", 6788.3),
@@ -456,6 +503,8 @@ def main():
                    "cycles": st2[-1][1], "relres": st2[-1][2],
                    "converged": all(x[0] == "ok" and x[2] < TOL for x in st2),
                    "dtype": "f64" if other == "fp64" else "f32+f64", **precision_opts(args, other)}
+        if other == "mixed":
+            variant["rooflines"] = mixed_rooflines(s2, stream, w["name"], dofs, w.get("nu", 5))
         s2.close()
 
     # ---- serving: continuous batching of the uneven forward/adjoint request trace ----

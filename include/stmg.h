@@ -238,6 +238,17 @@ stmg_status stmg_exact_solve(stmg_t handle, int level, int adjoint, const double
 /* One V-cycle of Alg. 1 on the finest level, u updated in place, in the precision of
  * the options (STMG_MIXED: one FP64 defect-correction step around one FP32 cycle). */
 stmg_status stmg_vcycle(stmg_t handle, int adjoint, double* u, const double* b);
+/* One step of the mixed scheme's V-cycle (Alg. 1 in FP32 inside FP64 defect correction) on
+ * the handle's own level vectors, enqueued on its stream without synchronising, so that the
+ * step can be timed on its own: kind 0 = level l's DOWN half (the nu pre-smoothing sweeps
+ * from zero, the residual and the restriction into level l+1), kind 1 = level l's UP half
+ * (prolongation of level l+1's correction and the nu post-smoothing sweeps; on level 0 added
+ * into the FP64 iterate), kind 2 = the FP64 defect of level 0 (the result is then read
+ * from the device's scalars, not returned).  The vectors hold whatever the last solve or
+ * V-cycle left in them (uninitialised before the first), and the FP64 iterate is modified.
+ * STMG_EINVAL unless the handle is STMG_MIXED with nu > 0, 0 <= level < levels - 1 and
+ * kind in 0..2 (kind 2: level 0 only). */
+stmg_status stmg_mixed_pass(stmg_t handle, int level, int adjoint, int kind);
 
 /* ---- allocation-free sensitivity ------------------------------------------------------ */
 /* The paper has no counterpart to this entry point; it is a deployment variant of

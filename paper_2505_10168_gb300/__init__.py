@@ -188,3 +188,10 @@ class Solver:
     def vcycle(self, u, b, adjoint=False):
         B.check(B.lib().stmg_vcycle(self._h, int(adjoint), B.ptr(u), B.ptr(b)), self._h)
         return u
+
+    MIXED_PASS_KINDS = {"down": 0, "up": 1, "defect": 2}
+
+    def mixed_pass(self, level, kind, adjoint=False):
+        """Enqueue one step of the mixed scheme on the solver's own vectors (``kind``: "down",
+        "up" or "defect"), without synchronising: for timing single passes."""
+        B.check(B.lib().stmg_mixed_pass(self._h, int(level), int(adjoint), self.MIXED_PASS_KINDS[kind]), self._h)

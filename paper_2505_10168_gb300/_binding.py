@@ -97,6 +97,7 @@ _SIGS = {
     "stmg_prolong_add": (_i, [_vp, _i, _vp, _vp]),
     "stmg_exact_solve": (_i, [_vp, _i, _i, _vp, _vp]),
     "stmg_vcycle": (_i, [_vp, _i, _vp, _vp]),
+    "stmg_mixed_pass": (_i, [_vp, _i, _i, _i]),
     "stmg_sensitivity_noalloc": (_i, [_i, _i, _d, _d, _vp, _dp, _vp, _vp, _vp, _vp]),
     "stmg_kernel_launches": (C.c_ulonglong, []),
     "stmg_set_stream": (_i, [_vp, _vp]),

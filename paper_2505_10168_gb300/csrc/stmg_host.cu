@@ -533,23 +533,15 @@ StreamArgs stream_args(const Level& L, double omega) {
   return a;
 }
 
-// Alg. 1 in FP32 with fused passes: on every level the nu pre-smoothing sweeps from a
-// zero start, the residual and the restriction run as one DOWN pass (or several when
-// nu > 5), and the prolongation plus the nu post-smoothing sweeps as one UP pass.  On the
-// finest level the result is added to the FP64 iterate u64 (mixed scheme) instead of
-// being stored.  The level's FP32 u pointer ends on the level's result.
-stmg_status vcycle32_fused(stmg_t h, int l, bool adj, double* u64, bool zero_start = true) {
+// The DOWN half of level l < last in FP32 fused passes: the nu pre-smoothing sweeps (from
+// zero, or on the finest level from the current FP32 iterate when an inner iteration
+// continues), the residual and the restriction into level l+1's b' (one pass, or several
+// when nu > 5).  Returns the buffer holding the level's smoothed iterate in *cur.
+stmg_status down32(stmg_t h, int l, bool adj, bool zero_start, float** cur) {
   Level& L = h->lev[l];
-  if (l == (int)h->lev.size() - 1) {
-    CK(exact_level<float>(h, L, adj, L.b32, L.u32));
-    if (u64) CK(launch_add_correction(L.nvec, u64, L.u32, kexp(h), h->s));
-    return STMG_OK;
-  }
   Level& C = h->lev[l + 1];
   const std::vector<int> passes = sweep_passes(h->o.nu);
   const bool xc = L.next == STMG_XCOARSEN;
-  // DOWN (from zero on coarse levels; on the finest level from the current FP32 iterate
-  // when the cycle continues an inner iteration)
   float* in = zero_start ? nullptr : L.u32;
   float* out = zero_start ? L.u32 : L.t32;
   for (size_t p = 0; p < passes.size(); ++p) {
@@ -570,8 +562,20 @@ stmg_status vcycle32_fused(stmg_t h, int l, bool adj, double* u64, bool zero_sta
     in = out;
     out = (out == L.u32) ? L.t32 : L.u32;
   }
-  CKS(vcycle32_fused(h, l + 1, adj, nullptr));
-  // UP
+  *cur = in;
+  return STMG_OK;
+}
+
+// The UP half of level l < last: prolongation of level l+1's correction added to the
+// iterate in `in`, then the nu post-smoothing sweeps; the result is added to the FP64
+// iterate u64 (scaled back by 2^-k) when u64 is set, else stored in a level buffer.  The
+// level's FP32 u pointer ends on the level's result.
+stmg_status up32(stmg_t h, int l, bool adj, float* in, double* u64) {
+  Level& L = h->lev[l];
+  Level& C = h->lev[l + 1];
+  const std::vector<int> passes = sweep_passes(h->o.nu);
+  const bool xc = L.next == STMG_XCOARSEN;
+  float* out = (in == L.u32) ? L.t32 : L.u32;
   for (size_t p = 0; p < passes.size(); ++p) {
     StreamArgs a = stream_args(L, h->o.omega);
     a.u_in = in;
@@ -597,6 +601,24 @@ stmg_status vcycle32_fused(stmg_t h, int l, bool adj, double* u64, bool zero_sta
   L.u32 = in;
   L.t32 = other;
   return STMG_OK;
+}
+
+// Alg. 1 in FP32 with fused passes: on every level the nu pre-smoothing sweeps from a
+// zero start, the residual and the restriction run as one DOWN pass (or several when
+// nu > 5), and the prolongation plus the nu post-smoothing sweeps as one UP pass.  On the
+// finest level the result is added to the FP64 iterate u64 (mixed scheme) instead of
+// being stored.  The level's FP32 u pointer ends on the level's result.
+stmg_status vcycle32_fused(stmg_t h, int l, bool adj, double* u64, bool zero_start = true) {
+  Level& L = h->lev[l];
+  if (l == (int)h->lev.size() - 1) {
+    CK(exact_level<float>(h, L, adj, L.b32, L.u32));
+    if (u64) CK(launch_add_correction(L.nvec, u64, L.u32, kexp(h), h->s));
+    return STMG_OK;
+  }
+  float* cur = nullptr;
+  CKS(down32(h, l, adj, zero_start, &cur));
+  CKS(vcycle32_fused(h, l + 1, adj, nullptr));
+  return up32(h, l, adj, cur, u64);
 }
 
 // Read one device double (after the stream's pending work).
@@ -647,7 +669,6 @@ stmg_status assemble_into(stmg_t h, const double* q, double* b) {
   return STMG_OK;
 }
 
-// ||b - J u||^2 on level 0 in FP64 (u null: ||b||^2).
 // The device int holding the scale exponent k of the finest level's FP32 arithmetic (see
 // scale_exp): the last of the handle's device scalars.
 int* kexp(stmg_t h) { return reinterpret_cast<int*>(h->scal + 7); }
@@ -1490,6 +1511,24 @@ stmg_status stmg_vcycle(stmg_t h, int adjoint, double* u, const double* b) {
   }
   CKS(copy_out(h, u, L.u, L.pitch, L.NT + 1, L.N + 1));
   CK(cudaStreamSynchronize(h->s));
+  return STMG_OK;
+}
+
+stmg_status stmg_mixed_pass(stmg_t h, int level, int adjoint, int kind) {
+  if (!h) return fail(nullptr, STMG_EINVAL, "NULL handle");
+  if (h->o.precision != STMG_MIXED || h->o.nu <= 0)
+    return fail(h, STMG_EINVAL, "stmg_mixed_pass needs the mixed scheme with nu > 0");
+  const int nl = (int)h->lev.size();
+  if (kind < 0 || kind > 2 || level < 0 || level >= nl - 1 || (kind == 2 && level != 0))
+    return fail(h, STMG_EINVAL, "stmg_mixed_pass: bad level %d or kind %d", level, kind);
+  Level& L = h->lev[level];
+  if (kind == 0) {
+    float* cur = nullptr;
+    return down32(h, level, adjoint != 0, true, &cur);
+  }
+  if (kind == 1) return up32(h, level, adjoint != 0, L.u32, level == 0 ? L.u : nullptr);
+  CK(launch_defect(view<double>(L, h->o.omega), L.cf32, adjoint != 0, L.u, L.b, kexp(h), L.b32, h->partials, h->scal,
+                   h->s));
   return STMG_OK;
 }
 

@@ -43,3 +43,4 @@ def test_default_opts_and_errors_without_gpu():
     assert b"nel" in lib.stmg_last_error(None)
     with pytest.raises(_binding.STMGError):
         _binding.make_opts(no_such_option=1)
+    assert _binding.STATUS[lib.stmg_mixed_pass(None, 0, 0, 0)] == "einval"

@@ -448,3 +448,30 @@ def test_full_size_config2_against_exact_solution(precision):
     print("config2 %s: cycles %d relres %.3e max rel err vs exact %.3e" % (precision, cyc, rr, err))
     assert err < 1e-5, err
     g.close()
+
+
+def test_mixed_pass_entry_point():
+    """stmg_mixed_pass enqueues single steps of the mixed scheme on the solver's own vectors
+    (for timing); it rejects other precisions, levels and kinds, and leaves the next cold
+    solve unchanged, bit for bit."""
+    N, NT, L, tT, k, c = _case(1)
+    g = pkg.Solver(N, NT, L, tT, T(k), T(c), precision="mixed", tol=1e-9, max_coarse_dofs=64)
+    b = T(_rand_vec(21, (NT + 1, N + 1)))
+    u0 = torch.empty_like(b)
+    st0 = g.solve(u0, b=b)
+    for kind in ("down", "up", "defect"):
+        for adj in (False, True):
+            g.mixed_pass(0, kind, adjoint=adj)
+    g.mixed_pass(g.num_levels - 2, "up")
+    torch.cuda.synchronize()
+    for lev, kind in ((g.num_levels - 1, "down"), (1, "defect"), (-1, "up")):
+        with pytest.raises(Exception):
+            g.mixed_pass(lev, kind)
+    u1 = torch.empty_like(b)
+    assert g.solve(u1, b=b) == st0
+    assert torch.equal(u0, u1)
+    g.close()
+    f = pkg.Solver(N, NT, L, tT, T(k), T(c), max_coarse_dofs=64)
+    with pytest.raises(Exception):
+        f.mixed_pass(0, "down")
+    f.close()
