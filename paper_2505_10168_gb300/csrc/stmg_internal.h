@@ -119,7 +119,7 @@ __device__ __forceinline__ double to_f64(float f, int k = 0) {
 // memory so that captured graphs read the current one): the FP32 copies of FP64 residuals
 // are scaled by 2^k, FP32 corrections are scaled back by 2^-k, and the FP32 termination
 // norms are taken of 2^k r and scaled back by 2^-2k.  k is chosen when ||b|| is summed,
-// so that 2^k b has an RMS in [1, 4): magnitudes of b far outside the FP32 range neither
+// so that 2^k b has an RMS in [1, 2): magnitudes of b far outside the FP32 range neither
 // flush to zero nor overflow.  In range, the result is independent of k (a power-of-two
 // scale commutes with every rounding).
 __device__ __forceinline__ int scale_exp(const int* kexp) { return kexp ? *kexp : 0; }
