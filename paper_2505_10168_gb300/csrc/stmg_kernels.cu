@@ -190,25 +190,43 @@ __global__ void __launch_bounds__(kThreads) k_restrict(int type, int Nf, int NTf
 
 // u += P z (Sec. 3.1): type 1, x: fine node 2j gets z_j, node 2j+1 gets (z_j + z_{j+1}) / 2;
 // type 2, t causal: fine rows 2m and 2m+1 get coarse row m; type 3, t bilinear: fine row
-// 2m gets z_m and row 2m+1 gets (z_m + z_{m+1}) / 2.
+// 2m gets z_m and row 2m+1 gets (z_m + z_{m+1}) / 2.  One thread per coarse DOF updates
+// both fine DOFs it feeds (nodes 2j, 2j+1 of a row, as one 2-vector, or rows 2m, 2m+1 of a
+// node), so each z is read once and an interpolated DOF costs one add and one FMA: on this
+// GPU FP64 additions run at the FMA rate, 1/64 of FP32, and one per DOF already takes
+// longer than the kernel's memory traffic.
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_prolong_add(int type, FastDiv fdf, uint32_t total, int pf,
-                                                          T* __restrict__ u, int pc, const T* __restrict__ z) {
+__global__ void __launch_bounds__(kThreads) k_prolong_add(int type, int Nf, int NTf, FastDiv fdc, uint32_t total,
+                                                          int pf, T* __restrict__ u, int pc, const T* __restrict__ z) {
   const uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= total) return;
-  int n, i;
-  split_index(idx, fdf, n, i);
-  T add;
+  int a, c;
+  split_index(idx, fdc, a, c);
   if (type == 1) {
-    const T* zr = z + (size_t)n * pc;
-    add = (i & 1) ? T(0.5) * (zr[i >> 1] + zr[(i >> 1) + 1]) : zr[i >> 1];
-  } else if (type == 2 || !(n & 1)) {
-    add = z[(size_t)(n >> 1) * pc + i];
+    // a: row n, c: coarse node j
+    const T* zr = z + (size_t)a * pc;
+    T* ur = u + (size_t)a * pf + 2 * c;
+    const T z0 = zr[c];
+    if (2 * c + 1 <= Nf) {
+      using V2 = typename std::conditional<std::is_same<T, double>::value, double2, float2>::type;
+      V2 v = *reinterpret_cast<V2*>(ur);
+      v.x = v.x + z0;
+      v.y = fma(T(0.5), z0 + zr[c + 1], v.y);
+      *reinterpret_cast<V2*>(ur) = v;
+    } else {
+      ur[0] = ur[0] + z0;
+    }
   } else {
-    // bilinear in time: fine row 2m+1 <- (z_m + z_{m+1}) / 2
-    add = T(0.5) * (z[(size_t)(n >> 1) * pc + i] + z[(size_t)((n >> 1) + 1) * pc + i]);
+    // a: coarse row m, c: node i
+    const T z0 = z[(size_t)a * pc + c];
+    T* u0 = u + (size_t)(2 * a) * pf + c;
+    u0[0] = u0[0] + z0;
+    if (2 * a + 1 <= NTf) {
+      T* u1 = u0 + pf;
+      if (type == 2) u1[0] = u1[0] + z0;
+      else u1[0] = fma(T(0.5), z0 + z[(size_t)(a + 1) * pc + c], u1[0]);
+    }
   }
-  u[(size_t)n * pf + i] += add;
 }
 
 // x <- (omega/D) x or (D/omega) x at every DOF (padding untouched).
@@ -717,10 +735,11 @@ cudaError_t launch_restrict(int type, int Nf, int NTf, int pf, const T* r, const
 template <typename T>
 cudaError_t launch_prolong_add(int type, int Nf, int NTf, int pf, T* u, int Nc, int NTc, int pc, const T* z,
                                cudaStream_t s) {
-  (void)Nc;
-  (void)NTc;
-  const uint32_t n = (uint32_t)((uint64_t)(NTf + 1) * (uint64_t)(Nf + 1));
-  k_prolong_add<T><<<blocks_for(n), kThreads, 0, s>>>(type, make_fastdiv(Nf + 1), n, pf, u, pc, z);
+  // one thread per coarse DOF: (row, coarse node) for x, (coarse row, node) for t
+  const int width = type == 1 ? Nc + 1 : Nf + 1;
+  const int rows = type == 1 ? NTf + 1 : NTc + 1;
+  const uint32_t n = (uint32_t)((uint64_t)rows * (uint64_t)width);
+  k_prolong_add<T><<<blocks_for(n), kThreads, 0, s>>>(type, Nf, NTf, make_fastdiv(width), n, pf, u, pc, z);
   count_launches(1);
   return cudaGetLastError();
 }
