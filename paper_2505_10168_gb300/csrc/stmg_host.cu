@@ -422,6 +422,12 @@ Vecs<double> vecs<double>(Level& L) { return {L.u, L.b, L.t}; }
 template <>
 Vecs<float> vecs<float>(Level& L) { return {L.u32, L.b32, L.t32}; }
 template <typename T>
+const T* coef(const Level& L);
+template <>
+const double* coef<double>(const Level& L) { return L.cf64; }
+template <>
+const float* coef<float>(const Level& L) { return L.cf32; }
+template <typename T>
 void set_u(Level& L, T* u);
 template <>
 void set_u<double>(Level& L, double* u) { L.u = u; }
@@ -497,9 +503,16 @@ stmg_status vcycle(stmg_t h, int l, bool adj, bool zero_init, bool first_done) {
   {
     Vecs<T> v = vecs<T>(L);
     Vecs<T> vc = vecs<T>(C);
-    if (L.gal) CK(gal_residual<T>(L, adj, v.u, v.b, v.t, h->s));
-    else CK(launch_residual<T>(view<T>(L, h->o.omega), adj, v.u, v.b, v.t, h->s));
-    CK(launch_restrict<T>(transfer_type(h->o, L), L.N, L.NT, L.pitch, v.t, view<T>(C, h->o.omega), vc.b, h->s));
+    if (!L.gal && !C.gal) {
+      // scaled residual, restricted with the folded scalings (kRW* slots)
+      CK(launch_residual_scaled<T>(view<T>(L, h->o.omega), adj, v.u, v.b, v.t, h->s));
+      CK(launch_restrict_scaled<T>(transfer_type(h->o, L), L.N, L.NT, L.pitch, coef<T>(L), (T)(L.W / C.W), v.t,
+                                   view<T>(C, h->o.omega), vc.b, h->s));
+    } else {
+      if (L.gal) CK(gal_residual<T>(L, adj, v.u, v.b, v.t, h->s));
+      else CK(launch_residual<T>(view<T>(L, h->o.omega), adj, v.u, v.b, v.t, h->s));
+      CK(launch_restrict<T>(transfer_type(h->o, L), L.N, L.NT, L.pitch, v.t, view<T>(C, h->o.omega), vc.b, h->s));
+    }
   }
   CKS(vcycle<T>(h, l + 1, adj, true, false));
   {
@@ -1023,6 +1036,13 @@ stmg_status build_hierarchy(stmg_t h, const std::vector<double>& hk, const std::
   for (Level& L : h->lev) CKS(setup_level(h, L));
   CKS(alloc_vectors(h));
   CKS(build_galerkin(h));
+  for (size_t l = 0; l + 1 < h->lev.size(); ++l) {
+    Level& L = h->lev[l];
+    const Level& C = h->lev[l + 1];
+    if (L.gal || C.gal) continue;
+    CK(launch_build_rweights(transfer_type(h->o, L), L.N, L.pitch, C.N, C.pitch, L.W, C.W, h->o.omega, C.cf64,
+                             L.cf64, L.cf32, h->s));
+  }
   CKS(build_scan_powers(h));
   CK(cudaStreamSynchronize(h->s));
   return STMG_OK;

@@ -40,6 +40,11 @@ enum CoefSlot {
   kW = 6,                                             // omega / D (b -> b')
   kDW = 7,                                            // D / omega (b' -> b)
   kSL = 8, kSU = 9, kSPL = 10, kSPC = 11, kSPR = 12,  // -omega c_k / D
+  // restriction toward the next level applied to the scaled residual y = (omega/D) r, with
+  // the fine (D/omega) and the coarse (omega/D_c) scalings folded in (launch_build_rweights):
+  // x, per coarse node j: weights of fine nodes 2j-1, 2j, 2j+1 (interior rows); t, per node
+  // i: kRWC for interior coarse rows, kRWR = kRWC / 2, kRWL for fine row 1 in coarse row 0
+  kRWL = 13, kRWC = 14, kRWR = 15,
   kNumCoef = 16
 };
 
@@ -165,6 +170,18 @@ cudaError_t launch_sweep(const LevelView<T>& lv, bool adj, const T* u, const T* 
 template <typename T>
 cudaError_t launch_sweep_norm(const LevelView<T>& lv, bool adj, const T* u, const T* bs, T* uo, const float* dw32,
                               const int* kexp, double* partials, double* out, cudaStream_t s);
+// The scaled residual y = (omega/D)(b - J u) = b' - omega u + sum S u (no unscaling).
+template <typename T>
+cudaError_t launch_residual_scaled(const LevelView<T>& lv, bool adj, const T* u, const T* bs, T* y, cudaStream_t s);
+// b'_c = R r from the scaled residual y with the fine level's kRW* weights (coef: the fine
+// level's coefficient table; r0 = W_f / W_c for x-restriction's Dirichlet row).
+template <typename T>
+cudaError_t launch_restrict_scaled(int type, int Nf, int NTf, int pf, const T* coef, T r0, const T* y,
+                                   const LevelView<T>& cv, T* bc, cudaStream_t s);
+// Fills the fine level's kRW* slots (FP64 and FP32 tables) for restriction type 1/2/3 toward
+// a coarse level with coefficient table cfc (pitch pc, Nc elements).
+cudaError_t launch_build_rweights(int type, int Nf, int pf, int Nc, int pc, double Wf, double Wc, double omega,
+                                  const double* cfc, double* cf64, float* cf32, cudaStream_t s);
 // r = b - J u from the stored b'.
 template <typename T>
 cudaError_t launch_residual(const LevelView<T>& lv, bool adj, const T* u, const T* bs, T* r, cudaStream_t s);

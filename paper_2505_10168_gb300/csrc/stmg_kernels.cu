@@ -153,7 +153,85 @@ __global__ void __launch_bounds__(kThreads) k_residual(LevelView<T> lv, uint32_t
   split_index(idx, lv.fd, n, i);
   const size_t p = (size_t)n * lv.pitch + i;
   if (MODE == 0) r[p] = unscale(lv, n, i) * scaled_residual<T, ADJ>(lv, u, bs, n, i, p);
+  else if (MODE == 2) r[p] = scaled_residual<T, ADJ>(lv, u, bs, n, i, p);
   else r[p] = apply_at(lv, ADJ, u, n, i, p);
+}
+
+// Restriction from the scaled residual y = (omega/D) r with the weights of the fine level's
+// kRW* slots, which fold D/omega of the fine node and omega/D_c of the coarse node into
+// P^T (the operator of k_restrict applied to r): x, b_c = wl y_{2j-1} + wc y_{2j} +
+// wr y_{2j+1}; t causal, b_c = a0 y_{2m} + a1 y_{2m+1}; t bilinear, b_c = a0 y_{2m} +
+// a1 (y_{2m-1} + y_{2m+1}).  Coarse row 0 (Dirichlet) takes its weights from r0 = W_f/W_c,
+// r0h = r0/2 and, for t, kRWL (fine row 1).  One arithmetic form per type with the weights
+// selected: a branch between forms would be if-converted into both, and on this GPU every
+// FP64 instruction costs 64 issue cycles of its unit.  The FP64 residual thereby drops its
+// unscaling multiply (6 FMAs per DOF instead of 7).
+template <typename T, int TYPE>
+__global__ void __launch_bounds__(kThreads) k_restrict_scaled(int Nf, int NTf, int pf, const T* cf, T r0, T r0h,
+                                                              const T* __restrict__ y, LevelView<T> cv,
+                                                              uint32_t total, T* __restrict__ bc) {
+  const uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  int m, j;
+  split_index(idx, cv.fd, m, j);
+  const bool dir = m == 0;
+  T out;
+  if (TYPE == 1) {
+    const T* row = y + (size_t)m * pf + 2 * j;
+    const T yc = row[0];
+    const T yl = j >= 1 ? row[-1] : T(0);
+    const T yr = 2 * j + 1 <= Nf ? row[1] : T(0);
+    const T wl = dir ? r0h : cf[kRWL * pf + j];
+    const T wc = dir ? r0 : cf[kRWC * pf + j];
+    const T wr = dir ? r0h : cf[kRWR * pf + j];
+    out = fma(wl, yl, fma(wr, yr, wc * yc));
+  } else {
+    const T* col = y + j;
+    const T y0 = col[(size_t)(2 * m) * pf];
+    const T y1 = 2 * m + 1 <= NTf ? col[(size_t)(2 * m + 1) * pf] : T(0);
+    const T wc = cf[kRWC * pf + j];
+    const T a0 = dir ? r0h : wc;
+    if (TYPE == 2) {
+      const T a1 = dir ? cf[kRWL * pf + j] : wc;
+      out = fma(a1, y1, a0 * y0);
+    } else {
+      const T a1 = dir ? cf[kRWL * pf + j] : cf[kRWR * pf + j];
+      const T am = dir ? T(0) : cf[kRWR * pf + j];
+      const T ym = dir ? T(0) : col[(size_t)(2 * m - 1) * pf];
+      out = fma(a1, y1, fma(am, ym, a0 * y0));
+    }
+  }
+  bc[(size_t)m * cv.pitch + j] = out;
+}
+
+// The kRW* weights of a fine level toward its coarse level (one thread per coarse node j
+// for x, per node i for t).  u_i = D_i/omega (W_f/omega at i = 0) is the fine kDW slot,
+// s_j = omega/D_c (omega/W_c at j = 0) the coarse kW slot.
+__global__ void k_build_rweights(int type, int Nf, int pf, int Nc, int pc, double Wf, double Wc, double omega,
+                                 const double* __restrict__ cfc, double* cf64, float* cf32) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  double wl, wc, wr;
+  if (type == 1) {
+    if (j > Nc) return;
+    const double sc = cfc[kW * pc + j];
+    wc = sc * cf64[kDW * pf + 2 * j];
+    wl = j >= 1 ? 0.5 * sc * cf64[kDW * pf + 2 * j - 1] : 0.0;
+    wr = 2 * j + 1 <= Nf ? 0.5 * sc * cf64[kDW * pf + 2 * j + 1] : 0.0;
+  } else {
+    // t: kRWC interior coarse rows, kRWR half of it (bilinear outer rows), kRWL fine row 1
+    // in coarse row 0 (fine row 0 there: W_f / (2 W_c), a kernel argument)
+    if (j > Nf) return;
+    const double ui = cf64[kDW * pf + j];
+    wc = 0.5 * cfc[kW * pc + j] * ui;
+    wr = 0.5 * wc;
+    wl = (type == 2 ? 0.5 : 0.25) * (omega / Wc) * ui;
+  }
+  cf64[kRWL * pf + j] = wl;
+  cf64[kRWC * pf + j] = wc;
+  cf64[kRWR * pf + j] = wr;
+  cf32[kRWL * pf + j] = (float)wl;
+  cf32[kRWC * pf + j] = (float)wc;
+  cf32[kRWR * pf + j] = (float)wr;
 }
 
 // Restriction b_c = s P^T r (Sec. 3.1), stored scaled by omega / D_c of the coarse level:
@@ -715,6 +793,36 @@ cudaError_t launch_residual(const LevelView<T>& lv, bool adj, const T* u, const 
 }
 
 template <typename T>
+cudaError_t launch_residual_scaled(const LevelView<T>& lv, bool adj, const T* u, const T* bs, T* y, cudaStream_t s) {
+  const uint32_t n = dofs(lv);
+  if (adj) k_residual<T, true, 2><<<blocks_for(n), kThreads, 0, s>>>(lv, n, u, bs, y);
+  else k_residual<T, false, 2><<<blocks_for(n), kThreads, 0, s>>>(lv, n, u, bs, y);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_restrict_scaled(int type, int Nf, int NTf, int pf, const T* coef, T r0, const T* y,
+                                   const LevelView<T>& cv, T* bc, cudaStream_t s) {
+  const uint32_t n = dofs(cv);
+  const T r0h = T(0.5) * r0;
+  if (type == 1) k_restrict_scaled<T, 1><<<blocks_for(n), kThreads, 0, s>>>(Nf, NTf, pf, coef, r0, r0h, y, cv, n, bc);
+  else if (type == 2)
+    k_restrict_scaled<T, 2><<<blocks_for(n), kThreads, 0, s>>>(Nf, NTf, pf, coef, r0, r0h, y, cv, n, bc);
+  else k_restrict_scaled<T, 3><<<blocks_for(n), kThreads, 0, s>>>(Nf, NTf, pf, coef, r0, r0h, y, cv, n, bc);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_build_rweights(int type, int Nf, int pf, int Nc, int pc, double Wf, double Wc, double omega,
+                                  const double* cfc, double* cf64, float* cf32, cudaStream_t s) {
+  const int n = (type == 1 ? Nc : Nf) + 1;
+  k_build_rweights<<<blocks_for(n), kThreads, 0, s>>>(type, Nf, pf, Nc, pc, Wf, Wc, omega, cfc, cf64, cf32);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_apply(const LevelView<T>& lv, bool adj, const T* u, T* y, cudaStream_t s) {
   const uint32_t n = dofs(lv);
   if (adj) k_residual<T, true, 1><<<blocks_for(n), kThreads, 0, s>>>(lv, n, u, nullptr, y);
@@ -874,6 +982,9 @@ cudaError_t launch_sens_final(int N, int chunks, const double* chi, Simp6 sp, co
                                             const int*, double*, double*,                                       \
                                             cudaStream_t);                                                        \
   template cudaError_t launch_residual<T>(const LevelView<T>&, bool, const T*, const T*, T*, cudaStream_t);       \
+  template cudaError_t launch_residual_scaled<T>(const LevelView<T>&, bool, const T*, const T*, T*, cudaStream_t); \
+  template cudaError_t launch_restrict_scaled<T>(int, int, int, int, const T*, T, const T*, const LevelView<T>&,  \
+                                                 T*, cudaStream_t);                                               \
   template cudaError_t launch_apply<T>(const LevelView<T>&, bool, const T*, T*, cudaStream_t);                    \
   template cudaError_t launch_restrict<T>(int, int, int, int, const T*, const LevelView<T>&, T*, cudaStream_t);   \
   template cudaError_t launch_prolong_add<T>(int, int, int, int, T*, int, int, int, const T*, cudaStream_t);      \
