@@ -281,19 +281,21 @@ __global__ void __launch_bounds__(kThreads) k_prolong_add(int type, int Nf, int 
   int a, c;
   split_index(idx, fdc, a, c);
   if (type == 1) {
-    // a: row n, c: coarse node j
+    // a: row n, c: coarse node j; the last coarse node feeds fine node N alone (one
+    // arithmetic form for both, so that no FP64 operation is duplicated by if-conversion)
+    using V2 = typename std::conditional<std::is_same<T, double>::value, double2, float2>::type;
     const T* zr = z + (size_t)a * pc;
     T* ur = u + (size_t)a * pf + 2 * c;
+    const bool pair = 2 * c + 1 <= Nf;
     const T z0 = zr[c];
-    if (2 * c + 1 <= Nf) {
-      using V2 = typename std::conditional<std::is_same<T, double>::value, double2, float2>::type;
-      V2 v = *reinterpret_cast<V2*>(ur);
-      v.x = v.x + z0;
-      v.y = fma(T(0.5), z0 + zr[c + 1], v.y);
-      *reinterpret_cast<V2*>(ur) = v;
-    } else {
-      ur[0] = ur[0] + z0;
-    }
+    const T z1 = pair ? zr[c + 1] : T(0);
+    V2 v;
+    if (pair) v = *reinterpret_cast<const V2*>(ur);
+    else v = V2{ur[0], T(0)};
+    v.x = v.x + z0;
+    v.y = fma(T(0.5), z0 + z1, v.y);
+    if (pair) *reinterpret_cast<V2*>(ur) = v;
+    else ur[0] = v.x;
   } else {
     // a: coarse row m, c: node i
     const T z0 = z[(size_t)a * pc + c];
