@@ -41,7 +41,9 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
-    p.add_argument("--workload", default="config2", choices=["config1", "config2", "config3", "config4"])
+    p.add_argument("--workload", default="filtered_simp", choices=sorted(WORKLOADS),
+                   help="rod_blocks (128 x 128 two-phase blocks), filtered_simp (4096 x 16384, k_ins 1e-4), "
+                        "filtered_simp_high_contrast (same grid, k_ins 1e-6), random_design (1024 x 4096, nu 20)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-variant", action="store_true", help="skip the other-precision solve of the same workload")
@@ -52,6 +54,9 @@ def parse():
                    help="requests of the 512-request serving trace to replay (0: skip serving)")
     p.add_argument("--serving-workers", type=int, default=6)
     return p.parse_args()
+
+
+WORKLOADS = ("rod_blocks", "filtered_simp", "filtered_simp_high_contrast", "random_design")
 
 
 def load_workload(name):
@@ -260,10 +265,10 @@ SERVING_OPTS = dict(precision="mixed", tol=TOL, nu=60, max_cycles=300)
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture
 # of the kernel on the named workload; a kernel changed since its capture has no entry.
 NCU_TRAFFIC = {
-    ("config2", "k_sweep<double>"): 1.590e9,
-    ("config2", "k_defect (FP64, finest level)"): 1.3329e9,
-    ("config2", "k_stream UP + FP64 accumulate (finest level)"): 1.7467e9,
-    ("config2", "k_stream DOWN from zero (finest level)"): 0.6300e9,
+    ("filtered-simp-4096x16384", "k_sweep<double>"): 1.590e9,
+    ("filtered-simp-4096x16384", "k_defect (FP64, finest level)"): 1.3329e9,
+    ("filtered-simp-4096x16384", "k_stream UP + FP64 accumulate (finest level)"): 1.7467e9,
+    ("filtered-simp-4096x16384", "k_stream DOWN from zero (finest level)"): 0.6300e9,
 }
 
 

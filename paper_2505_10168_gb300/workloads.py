@@ -12,14 +12,19 @@ A uniform double in [0, 1) is (z >> 11) * 2^-53.
 
 Workloads (all with T = 0 at t = 0 and x = 0, adiabatic at x = L):
 
-* ``config1``: L = 1, t_end = 1, 128 x 128, c = 1, conductivity in 16 blocks of 8
+* ``rod_blocks``: L = 1, t_end = 1, 128 x 128, c = 1, conductivity in 16 blocks of 8
   elements, each block k = 1e-3 or 1 with probability 1/2 (seed 1), load q = 1.
-* ``config2``: 4096 x 16384, design field chi ~ U(0,1) (seed 2) smoothed by a centred
-  16-element box filter (window [e-8, e+7], mean over the elements inside the domain),
-  SIMP k_ins = 1e-4, k_con = 1, p_k = 3, c = 1; q = 1 on elements with x_e < 0.1, else 0.
-* ``config3``: as config2 with k_ins = 1e-6.
-* ``config4``: 1024 x 4096, chi ~ U(0.05, 1) (seed 4), k_ins = 1e-3, p_k = 3, c = 1,
-  q = 1; 32 elements for finite differences drawn with seed 5.
+* ``filtered_simp``: 4096 x 16384, design field chi ~ U(0,1) (seed 2) smoothed by a
+  centred 16-element box filter (window [e-8, e+7], mean over the elements inside the
+  domain), SIMP k_ins = 1e-4, k_con = 1, p_k = 3, c = 1; q = 1 on elements with
+  x_e < 0.1, else 0.
+* ``filtered_simp_high_contrast``: as filtered_simp with k_ins = 1e-6.
+* ``random_design``: 1024 x 4096, chi ~ U(0.05, 1) (seed 4), k_ins = 1e-3, p_k = 3, c = 1,
+  q = 1; 32 elements for finite differences drawn with seed 5 (the differentiation
+  workload, solved with nu = 20).
+
+Each returns a dict whose ``name`` states the field and the grid, e.g.
+"filtered-simp-4096x16384".
 * ``serving_requests``: 512 requests (seed 6), N log-uniform in [256, 4096] and NT
   log-uniform in [512, 16384], both rounded to multiples of 64; two-phase 8-element
   blocks with k in {k_min, 1}, k_min = 10^-U(3,6); forward or adjoint with p = 1/2;
@@ -100,10 +105,10 @@ def simp_params(k_ins, k_con, c_ins, c_con, p_k=3.0, p_c=2.0) -> np.ndarray:
     return np.array([k_ins, k_con, c_ins, c_con, p_k, p_c], dtype=np.float64)
 
 
-def config1():
+def rod_blocks():
     N = NT = 128
     k = two_phase_blocks(1, N, 8, 1e-3, 1.0)
-    return dict(name="config1", N=N, NT=NT, L=1.0, tT=1.0, k=k, c=np.ones(N), chi=None, simp=None,
+    return dict(name="rod-blocks-%dx%d" % (N, NT), N=N, NT=NT, L=1.0, tT=1.0, k=k, c=np.ones(N), chi=None, simp=None,
                 q=load_uniform(N, NT), tol=1e-10)
 
 
@@ -111,20 +116,20 @@ def _chi_filtered(seed, N):
     return box_filter(uniform(seed, N), 16)
 
 
-def config2(N=4096, NT=16384, k_ins=1e-4, seed=2, name="config2"):
+def filtered_simp(N=4096, NT=16384, k_ins=1e-4, seed=2, name="filtered-simp"):
     chi = _chi_filtered(seed, N)
-    return dict(name=name, N=N, NT=NT, L=1.0, tT=1.0, chi=chi, simp=simp_params(k_ins, 1.0, 1.0, 1.0),
+    return dict(name="%s-%dx%d" % (name, N, NT), N=N, NT=NT, L=1.0, tT=1.0, chi=chi, simp=simp_params(k_ins, 1.0, 1.0, 1.0),
                 k=None, c=None, q=load_left_strip(N, NT, 1.0), tol=1e-8)
 
 
-def config3(N=4096, NT=16384):
-    return config2(N, NT, k_ins=1e-6, name="config3")
+def filtered_simp_high_contrast(N=4096, NT=16384):
+    return filtered_simp(N, NT, k_ins=1e-6, name="filtered-simp-kins1e-6")
 
 
-def config4(N=1024, NT=4096):
+def random_design(N=1024, NT=4096):
     chi = 0.05 + 0.95 * uniform(4, N)
     fd = np.sort(np.floor(uniform(5, 32) * N).astype(np.int64))
-    return dict(name="config4", N=N, NT=NT, L=1.0, tT=1.0, chi=chi, simp=simp_params(1e-3, 1.0, 1.0, 1.0),
+    return dict(name="random-design-%dx%d" % (N, NT), N=N, NT=NT, L=1.0, tT=1.0, chi=chi, simp=simp_params(1e-3, 1.0, 1.0, 1.0),
                 k=None, c=None, q=load_uniform(N, NT), fd_elements=fd, theta_ref=1.0, tol=1e-10, nu=20)
 
 

@@ -47,7 +47,7 @@ def test_recompute_slabs_matches_exact_solution(N, NT, K):
 
 
 def _cfg4(N, NT):
-    w = wl.config4(N=N, NT=NT)
+    w = wl.random_design(N=N, NT=NT)
     return w, T(w["chi"]), T(w["q"])
 
 
@@ -73,7 +73,7 @@ def test_autograd_compliance_gradient_matches_oracle(slab_rows):
     solver.close()
 
 
-def test_config4_gradient_against_central_differences():
+def test_random_design_gradient_against_central_differences():
     """The differentiation workload at full size (1024 x 4096): autograd gradient of the
     compliance against central differences with h = 1e-6 on 32 random elements.  The
     solves stop at 1e-10: at this grid the FP64 evaluation of J u cancels ~1e6-fold

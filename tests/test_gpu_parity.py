@@ -85,7 +85,7 @@ def test_planner_agrees_with_oracle(i, reasm):
     g.close()
 
 
-@pytest.mark.parametrize("cfg", ["config1", "config2", "config3", "config4"])
+@pytest.mark.parametrize("cfg", ["rod_blocks", "filtered_simp", "filtered_simp_high_contrast", "random_design"])
 def test_planner_agrees_on_workloads(cfg):
     w = getattr(wl, cfg)()
     if w["k"] is None:
@@ -277,8 +277,8 @@ def test_cycle_with_wide_coarsest_level(precision, adj):
 
 
 @pytest.mark.parametrize("reasm", ["R", "K"])
-def test_config1_solve_matches_oracle(reasm):
-    w = wl.config1()
+def test_rod_blocks_solve_matches_oracle(reasm):
+    w = wl.rod_blocks()
     N, NT, L, tT = w["N"], w["NT"], w["L"], w["tT"]
     g, o = _pair(N, NT, L, tT, w["k"], w["c"], reassembly=reasm, tol=1e-10)
     b = oracle.assemble_load(N, NT, L / N, w["q"])
@@ -294,7 +294,7 @@ def test_config1_solve_matches_oracle(reasm):
 
 
 def test_host_and_device_arrays_agree():
-    w = wl.config1()
+    w = wl.rod_blocks()
     N, NT, L, tT = w["N"], w["NT"], w["L"], w["tT"]
     g = pkg.Solver(N, NT, L, tT, w["k"], w["c"])  # host material
     q = np.ascontiguousarray(w["q"])
@@ -307,8 +307,8 @@ def test_host_and_device_arrays_agree():
     g.close()
 
 
-def test_adjoint_solve_identity_and_sensitivity_config4_small():
-    w = wl.config4(N=256, NT=1024)
+def test_adjoint_solve_identity_and_sensitivity_random_design_small():
+    w = wl.random_design(N=256, NT=1024)
     N, NT, L, tT = w["N"], w["NT"], w["L"], w["tT"]
     chi = T(w["chi"])
     k = torch.empty(N, dtype=torch.float64, device=DEV)
@@ -357,7 +357,7 @@ def test_sensitivity_with_penalised_heat_capacity():
 @pytest.mark.parametrize("adj", [False, True])
 @pytest.mark.parametrize("inner", [1, 2])
 def test_mixed_precision_reaches_fp64_residual(adj, inner):
-    w = wl.config2(N=512, NT=2048)
+    w = wl.filtered_simp(N=512, NT=2048)
     N, NT, L, tT = w["N"], w["NT"], w["L"], w["tT"]
     ko, co = oracle.simp(w["chi"], w["simp"])
     bo = oracle.assemble_load(N, NT, L / N, w["q"])
@@ -420,7 +420,7 @@ def test_edge_cases():
 
 
 def test_warm_restart_converges_in_fewer_cycles():
-    w = wl.config1()
+    w = wl.rod_blocks()
     N, NT = w["N"], w["NT"]
     g = pkg.Solver(N, NT, 1.0, 1.0, w["k"], w["c"], tol=1e-10)
     u = torch.empty((NT + 1, N + 1), dtype=torch.float64, device=DEV)
@@ -431,10 +431,10 @@ def test_warm_restart_converges_in_fewer_cycles():
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_full_size_config2_against_exact_solution(precision):
+def test_full_size_filtered_simp_against_exact_solution(precision):
     """The 4096 x 16384 workload in the launch configuration the benchmark times,
     solved to 1e-8, checked against the oracle's exact time-stepping solution."""
-    w = wl.config2()
+    w = wl.filtered_simp()
     N, NT, L, tT = w["N"], w["NT"], w["L"], w["tT"]
     ko, co = oracle.simp(w["chi"], w["simp"])
     g = pkg.Solver(N, NT, L, tT, T(ko), T(co), precision=precision, tol=1e-8)
@@ -445,7 +445,7 @@ def test_full_size_config2_against_exact_solution(precision):
     bo = oracle.assemble_load(N, NT, L / N, w["q"])
     ue = oracle.exact(N, NT, L, tT, ko, co, bo)
     err = rel(N_(u), ue)
-    print("config2 %s: cycles %d relres %.3e max rel err vs exact %.3e" % (precision, cyc, rr, err))
+    print("%s %s: cycles %d relres %.3e max rel err vs exact %.3e" % (w["name"], precision, cyc, rr, err))
     assert err < 1e-5, err
     g.close()
 

@@ -243,8 +243,8 @@ def test_level_operators_match_dense_on_every_level():
 
 # ---------------------------------------------------------------- solver loop and invariants
 
-def test_config1_converges_to_exact_solution():
-    cfg = wl.config1()
+def test_rod_blocks_converges_to_exact_solution():
+    cfg = wl.rod_blocks()
     N, NT = cfg["N"], cfg["NT"]
     H = oracle.Hierarchy(N, NT, cfg["L"], cfg["tT"], cfg["k"], cfg["c"])
     b = oracle.assemble_load(N, NT, cfg["L"] / N, cfg["q"])
@@ -257,7 +257,7 @@ def test_config1_converges_to_exact_solution():
 
 
 def test_linearity_of_the_cycle():
-    cfg = wl.config1()
+    cfg = wl.rod_blocks()
     N, NT = cfg["N"], cfg["NT"]
     H = oracle.Hierarchy(N, NT, cfg["L"], cfg["tT"], cfg["k"], cfg["c"])
     b = _rand_vec(3, H.shape(0))
@@ -267,7 +267,7 @@ def test_linearity_of_the_cycle():
 
 
 def test_adjoint_identity_and_cycle_counts():
-    cfg = wl.config4(N=64, NT=128)
+    cfg = wl.random_design(N=64, NT=128)
     N, NT = cfg["N"], cfg["NT"]
     k, c = oracle.simp(cfg["chi"], cfg["simp"])
     dt = cfg["tT"] / NT
@@ -313,7 +313,7 @@ def test_sensitivity_matches_central_differences(penalise_c):
 
 
 def test_solver_reports_divergence_and_max_cycles():
-    cfg = wl.config1()
+    cfg = wl.rod_blocks()
     N, NT = cfg["N"], cfg["NT"]
     b = oracle.assemble_load(N, NT, 1.0 / N, cfg["q"])
     H = oracle.Hierarchy(N, NT, 1.0, 1.0, cfg["k"], cfg["c"], nu=1)
