@@ -664,7 +664,8 @@ bool is_device_ptr(const void* p) {
 }
 
 // Element loads -> nodal b on level 0.
-stmg_status assemble_into(stmg_t h, const double* q, double* b) {
+// with_norm: also ||b||^2 into the handle's first device scalar and the FP32 scale exponent.
+stmg_status assemble_into(stmg_t h, const double* q, double* b, bool with_norm = false) {
   Level& L = h->lev[0];
   const double* qd = q;
   if (!is_device_ptr(q)) {
@@ -678,7 +679,10 @@ stmg_status assemble_into(stmg_t h, const double* q, double* b) {
     CK(cudaMemcpyAsync(h->qstage, q, n * sizeof(double), cudaMemcpyDefault, h->s));
     qd = h->qstage;
   }
-  CK(launch_assemble_load(view<double>(L, h->o.omega), L.dx, qd, b, h->s));
+  if (with_norm)
+    CK(launch_assemble_load(view<double>(L, h->o.omega), L.dx, qd, b, h->s, 0.0, 1.0, h->partials, h->scal, kexp(h)));
+  else
+    CK(launch_assemble_load(view<double>(L, h->o.omega), L.dx, qd, b, h->s));
   return STMG_OK;
 }
 
@@ -752,13 +756,16 @@ void normalize_level0(stmg_t h) {
 // sweep's input, still intact in the other ping-pong buffer.
 // Mixed: r = b - J u in FP64 (also the scaled FP32 right-hand side), one FP32 V-cycle
 // from zero on J e = r, u += e.
-stmg_status solve_loop(stmg_t h, bool adj, bool warm, int* cycles_out, double* relres_out) {
+stmg_status solve_loop(stmg_t h, bool adj, bool warm, int* cycles_out, double* relres_out, bool nb2_ready = false) {
   Level& L = h->lev[0];
   const stmg_opts& o = h->o;
   const LevelView<double> lv = view<double>(L, o.omega);
   if (!warm) CK(cudaMemsetAsync(L.u, 0, L.nvec * sizeof(double), h->s));
   double nb2 = 0.0;
-  CKS(resnorm2(h, adj, nullptr, L.b, &nb2, true));
+  // ||b||^2 and the FP32 scale exponent: already on the device when the load assembly
+  // formed them (nb2_ready), else from the stored b'
+  if (nb2_ready) CKS(read_scalar(h, h->scal, &nb2));
+  else CKS(resnorm2(h, adj, nullptr, L.b, &nb2, true));
   int cycles = 0;
   double rel = 0.0;
   stmg_status st = STMG_EMAXITER;
@@ -1283,13 +1290,13 @@ static stmg_status solve_common(stmg_t h, bool adj, const double* q_el, const do
   Level& L = h->lev[0];
   normalize_level0(h);
   if (q_el) {
-    CKS(assemble_into(h, q_el, L.b));
+    CKS(assemble_into(h, q_el, L.b, true));
   } else {
     CKS(copy_in(h, L.b, L.pitch, b_nodal, L.NT + 1, L.N + 1));
     CK(launch_scale<double>(view<double>(L, h->o.omega), true, L.b, h->s));
   }
   if (warm) CKS(copy_in(h, L.u, L.pitch, u, L.NT + 1, L.N + 1));
-  stmg_status st = solve_loop(h, adj, warm != 0, cycles, relres);
+  stmg_status st = solve_loop(h, adj, warm != 0, cycles, relres, q_el != nullptr);
   if (st != STMG_OK && st != STMG_EDIVERGED && st != STMG_EMAXITER) return st;
   CKS(copy_out(h, u, L.u, L.pitch, L.NT + 1, L.N + 1));
   CK(cudaStreamSynchronize(h->s));
@@ -1562,8 +1569,8 @@ stmg_status stmg_solve_resident(stmg_t h, bool adj, const double* q_dev, double 
   Level& L = h->lev[0];
   const LevelView<double> lv = view<double>(L, h->o.omega);
   normalize_level0(h);
-  CK(launch_assemble_load(lv, L.dx, q_dev, L.b, h->s, q_value, rhs_scale));
-  stmg_status st = solve_loop(h, adj, false, cycles, relres);
+  CK(launch_assemble_load(lv, L.dx, q_dev, L.b, h->s, q_value, rhs_scale, h->partials, h->scal, kexp(h)));
+  stmg_status st = solve_loop(h, adj, false, cycles, relres, true);
   if (st != STMG_OK && st != STMG_EDIVERGED && st != STMG_EMAXITER) return st;
   if (theta) {
     CK(cudaMemcpyAsync(L.t, L.b, L.nvec * sizeof(double), cudaMemcpyDeviceToDevice, h->s));

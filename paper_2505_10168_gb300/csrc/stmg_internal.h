@@ -237,9 +237,11 @@ struct Simp6 {
 };
 cudaError_t launch_simp(int N, const double* chi, Simp6 sp, double* k, double* c, cudaStream_t s);
 // b' = mult (omega/D) B b_Neu from element loads q[(NT+1) x N] (dense; nullptr: the
-// constant qconst on every element) into the padded layout.
+// constant qconst on every element) into the padded layout; with partials (kNormBlocks
+// entries), also ||b||^2 into out[0] and, with kset, the FP32 scale exponent from it.
 cudaError_t launch_assemble_load(const LevelView<double>& lv, double dx, const double* q, double* bs, cudaStream_t s,
-                                 double qconst = 0.0, double mult = 1.0);
+                                 double qconst = 0.0, double mult = 1.0, double* partials = nullptr,
+                                 double* out = nullptr, int* kset = nullptr);
 // ---- Galerkin reassembly (P-method, Sec. 5.1; stmg_galerkin.cu) ----
 // Level operator in row-class form: time row n uses coefficient set cls[n];
 // co[(c * 9 + (d + 1) * 3 + (e + 1)) * (N + 1) + i] is the coefficient of u(n + d, i + e) in

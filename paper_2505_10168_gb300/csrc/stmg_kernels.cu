@@ -688,26 +688,39 @@ __global__ void k_simp(int N, const double* __restrict__ chi, Simp6 sp, double* 
 // scaled as b' = mult (omega/D) b; q == nullptr: the same constant qconst on every element.
 // Writes every value of the padded rows.  Threads own columns and loop over rows, so the
 // column factor f (omega/D_i) with f = mult dx / 2 is formed once per thread and a DOF costs
-// one FP64 add and one multiply (none for a constant load).
+// one FP64 add and one multiply (none for a constant load).  partials: also ||b||^2, as
+// f^2 sum (q_{i-1} + q_i)^2 over the interior DOFs (b is zero on the Dirichlet DOFs), one
+// FMA per DOF, one partial per block.
 __global__ void __launch_bounds__(kThreads) k_assemble_load(LevelView<double> lv, const double* __restrict__ q,
-                                                            double qconst, double f, double* __restrict__ b) {
+                                                            double qconst, double f, double* __restrict__ b,
+                                                            double* __restrict__ partials) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= lv.pitch) return;
   const int N = lv.N;
-  const bool interior = i >= 1 && i <= N;
-  const double g = interior ? f * lv.coef[kW * lv.pitch + i] : 0.0;
-  const double vconst = g * (i < N ? 2.0 * qconst : qconst);
-  for (int n = blockIdx.y; n <= lv.NT; n += gridDim.y) {
-    double v = 0.0;
-    if (n >= 1 && interior) {
-      if (q) {
-        const double* qn = q + (size_t)n * N;
-        v = g * (qn[i - 1] + (i < N ? qn[i] : 0.0));
-      } else {
-        v = vconst;
+  double acc = 0.0;
+  if (i < lv.pitch) {
+    const bool interior = i >= 1 && i <= N;
+    const double g = interior ? f * lv.coef[kW * lv.pitch + i] : 0.0;
+    const double qc = i < N ? 2.0 * qconst : qconst;
+    const double vconst = g * qc;
+    for (int n = blockIdx.y; n <= lv.NT; n += gridDim.y) {
+      double v = 0.0;
+      if (n >= 1 && interior) {
+        double qs = qc;
+        if (q) {
+          const double* qn = q + (size_t)n * N;
+          qs = qn[i - 1] + (i < N ? qn[i] : 0.0);
+          v = g * qs;
+        } else {
+          v = vconst;
+        }
+        if (partials) acc = fma(qs, qs, acc);
       }
+      b[(size_t)n * lv.pitch + i] = v;
     }
-    b[(size_t)n * lv.pitch + i] = v;
+  }
+  if (partials) {
+    const double sum = block_sum<kThreads>(acc);
+    if (threadIdx.x == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = f * f * sum;
   }
 }
 
@@ -957,12 +970,23 @@ cudaError_t launch_simp(int N, const double* chi, Simp6 sp, double* k, double* c
 }
 
 cudaError_t launch_assemble_load(const LevelView<double>& lv, double dx, const double* q, double* bs,
-                                 cudaStream_t s, double qconst, double mult) {
-  // about 8 blocks per SM of 152, each thread looping over its column's rows
+                                 cudaStream_t s, double qconst, double mult, double* partials, double* out,
+                                 int* kset) {
+  // about 8 blocks per SM of 152 (at most kNormBlocks with the norm), each thread looping
+  // over its column's rows; the norm is fused while one partial per block fits the
+  // kNormBlocks-entry buffer (rows of at most 155 k columns), else it is a pass of its own
   const unsigned gx = blocks_for(lv.pitch);
-  const unsigned gy = (unsigned)std::max(1, std::min(lv.NT + 1, (int)((152 * 8 + gx - 1) / gx)));
-  k_assemble_load<<<dim3(gx, gy), kThreads, 0, s>>>(lv, q, qconst, mult * 0.5 * dx, bs);
+  const bool fuse = partials && gx <= (unsigned)kNormBlocks;
+  const int cap = fuse ? kNormBlocks : 152 * 8;
+  const unsigned gy = (unsigned)std::max(1, std::min(lv.NT + 1, (int)(cap / gx)));
+  k_assemble_load<<<dim3(gx, gy), kThreads, 0, s>>>(lv, q, qconst, mult * 0.5 * dx, bs, fuse ? partials : nullptr);
   count_launches(1);
+  if (fuse) {
+    k_final_sum<<<1, 1024, 0, s>>>(partials, (int)(gx * gy), out, nullptr, kset, (double)dofs(lv));
+    count_launches(1);
+  } else if (partials) {
+    return launch_resnorm<double>(lv, false, nullptr, bs, partials, out, s, kset);
+  }
   return cudaGetLastError();
 }
 
