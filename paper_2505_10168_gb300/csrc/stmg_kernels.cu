@@ -938,7 +938,9 @@ cudaError_t launch_defect(const LevelView<double>& lv, const float* coef32, bool
 
 cudaError_t launch_rhs32(const LevelView<double>& lv, const double* bs, const int* kexp, float* ys32,
                          cudaStream_t s) {
-  k_defect<false, true><<<kNormBlocks, kThreads, 0, s>>>(lv, dofs(lv), nullptr, nullptr, bs, kexp, ys32, nullptr);
+  // no reduction: one thread per DOF (the fixed reduction grid leaves too few loads in flight)
+  const uint32_t n = dofs(lv);
+  k_defect<false, true><<<blocks_for(n), kThreads, 0, s>>>(lv, n, nullptr, nullptr, bs, kexp, ys32, nullptr);
   count_launches(1);
   return cudaGetLastError();
 }
