@@ -573,8 +573,7 @@ __global__ void __launch_bounds__(kThreads) k_resnorm(LevelView<T> lv, uint32_t 
 // next FP32 cycle.  The squared norm, which only feeds the termination test, is accumulated
 // in FP32 per thread (2^k r = (D/omega) 2^k y with the FP32 coefficients) and summed in FP64
 // across the block: 6 FP64 FMAs per DOF (the conversion to FP32 runs on the integer pipe).
-// ZERO: u = 0, so y = b' (no FP64 arithmetic; the norm is not formed).
-template <bool ADJ, bool ZERO>
+template <bool ADJ>
 __global__ void __launch_bounds__(kThreads) k_defect(LevelView<double> lv, uint32_t total, const float* __restrict__ dw32,
                                                      const double* __restrict__ u, const double* __restrict__ bs,
                                                      const int* __restrict__ kexp, float* __restrict__ ys32,
@@ -586,18 +585,24 @@ __global__ void __launch_bounds__(kThreads) k_defect(LevelView<double> lv, uint3
     int n, i;
     split_index(idx, lv.fd, n, i);
     const size_t p = (size_t)n * lv.pitch + i;
-    if (ZERO) {
-      ys32[p] = to_f32_trunc(bs[p], k);
-      continue;
-    }
     const float y = to_f32_trunc(scaled_residual<double, ADJ>(lv, u, bs, n, i, p), k);
     ys32[p] = y;
     const float r = ((n == 0 || i == 0) ? Wo32 : dw32[i]) * y;
     acc = fmaf(r, r, acc);
   }
-  if (ZERO) return;
   const double s = block_sum<kThreads>((double)acc);
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+// y = 2^k b' truncated to FP32 over a whole padded array, two values per thread: the
+// mixed scheme's first defect from u = 0 (k from scale_exp).
+__global__ void __launch_bounds__(kThreads) k_to_f32_pairs(size_t n2, const double2* __restrict__ b,
+                                                           const int* __restrict__ kexp, float2* __restrict__ y) {
+  const size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (j >= n2) return;
+  const int k = scale_exp(kexp);
+  const double2 v = b[j];
+  y[j] = make_float2(to_f32_trunc(v.x, k), to_f32_trunc(v.y, k));
 }
 
 // Sum of the per-block partials into out[0].  kget: the partials are of 2^k r (k from
@@ -929,8 +934,8 @@ cudaError_t launch_defect(const LevelView<double>& lv, const float* coef32, bool
                           cudaStream_t s) {
   const uint32_t n = dofs(lv);
   const float* dw32 = coef32 + (size_t)kDW * lv.pitch;
-  if (adj) k_defect<true, false><<<kNormBlocks, kThreads, 0, s>>>(lv, n, dw32, u, bs, kexp, ys32, partials);
-  else k_defect<false, false><<<kNormBlocks, kThreads, 0, s>>>(lv, n, dw32, u, bs, kexp, ys32, partials);
+  if (adj) k_defect<true><<<kNormBlocks, kThreads, 0, s>>>(lv, n, dw32, u, bs, kexp, ys32, partials);
+  else k_defect<false><<<kNormBlocks, kThreads, 0, s>>>(lv, n, dw32, u, bs, kexp, ys32, partials);
   k_final_sum<<<1, 1024, 0, s>>>(partials, kNormBlocks, out, kexp, nullptr, 0.0);
   count_launches(2);
   return cudaGetLastError();
@@ -938,9 +943,10 @@ cudaError_t launch_defect(const LevelView<double>& lv, const float* coef32, bool
 
 cudaError_t launch_rhs32(const LevelView<double>& lv, const double* bs, const int* kexp, float* ys32,
                          cudaStream_t s) {
-  // no reduction: one thread per DOF (the fixed reduction grid leaves too few loads in flight)
-  const uint32_t n = dofs(lv);
-  k_defect<false, true><<<blocks_for(n), kThreads, 0, s>>>(lv, n, nullptr, nullptr, bs, kexp, ys32, nullptr);
+  // the whole padded array in pairs (the padding of b' is zero, and so becomes that of y)
+  const size_t n2 = (size_t)(lv.NT + 1) * lv.pitch / 2;
+  k_to_f32_pairs<<<blocks_for((long long)n2), kThreads, 0, s>>>(n2, reinterpret_cast<const double2*>(bs), kexp,
+                                                                reinterpret_cast<float2*>(ys32));
   count_launches(1);
   return cudaGetLastError();
 }
