@@ -134,13 +134,20 @@ struct Coefs {
 // (time level 0), whose row of J is W_Diri I.  px is the stage input of the previous row
 // (the next row for J^T), zero where the stencil has no such coupling; pl, pr are its
 // x-neighbours across the lane boundary, which that row's own stage shuffled and handed on.
-// hl, hr receive this row's shuffled neighbours of x for the next row.
+// hl, hr receive this row's shuffled neighbours of x for the next row.  The two terms whose
+// operands are column-aligned (a x + b' and the previous row's centre) run as packed FP32
+// pairs, one instruction for two columns; the four shifted-neighbour terms stay scalar.
 template <bool DIR, int V>
 __device__ __forceinline__ Vf<V> stage(float a, const Vf<V>& x, const Vf<V>& px, float pl, float pr, float& hl,
                                        float& hr, const Vf<V>& b, const Coefs<V>& cf) {
   Vf<V> o;
+  const float2 a2 = make_float2(a, a);
 #pragma unroll
-  for (int j = 0; j < V; ++j) o.e[j] = fmaf(a, x.e[j], b.e[j]);
+  for (int q = 0; q < V / 2; ++q) {
+    const float2 t = __ffma2_rn(a2, make_float2(x.e[2 * q], x.e[2 * q + 1]), make_float2(b.e[2 * q], b.e[2 * q + 1]));
+    o.e[2 * q] = t.x;
+    o.e[2 * q + 1] = t.y;
+  }
   if (DIR) {
     hl = 0.f;
     hr = 0.f;
@@ -153,6 +160,13 @@ __device__ __forceinline__ Vf<V> stage(float a, const Vf<V>& x, const Vf<V>& px,
   hl = xl;
   hr = xr;
 #pragma unroll
+  for (int q = 0; q < V / 2; ++q) {
+    const float2 c = __ffma2_rn(make_float2(cf.spc.e[2 * q], cf.spc.e[2 * q + 1]),
+                                make_float2(px.e[2 * q], px.e[2 * q + 1]), make_float2(o.e[2 * q], o.e[2 * q + 1]));
+    o.e[2 * q] = c.x;
+    o.e[2 * q + 1] = c.y;
+  }
+#pragma unroll
   for (int j = 0; j < V; ++j) {
     const float left = j == 0 ? xl : x.e[j - 1];
     const float right = j == V - 1 ? xr : x.e[j + 1];
@@ -161,7 +175,6 @@ __device__ __forceinline__ Vf<V> stage(float a, const Vf<V>& x, const Vf<V>& px,
     float t = fmaf(cf.sl.e[j], left, o.e[j]);
     t = fmaf(cf.su.e[j], right, t);
     t = fmaf(cf.spl.e[j], pleft, t);
-    t = fmaf(cf.spc.e[j], px.e[j], t);
     o.e[j] = fmaf(cf.spr.e[j], pright, t);
   }
   return o;
