@@ -101,6 +101,17 @@ __device__ __forceinline__ void stg_v(float* p, const Vf<V>& v) {
     reinterpret_cast<float4*>(p)[q] = make_float4(v.e[4 * q], v.e[4 * q + 1], v.e[4 * q + 2], v.e[4 * q + 3]);
 }
 
+// Columns 2q, 2q+1 of a lane's vector as a pair (for packed FP32 arithmetic) and back.
+template <int V>
+__device__ __forceinline__ float2 pair(const Vf<V>& v, int q) {
+  return make_float2(v.e[2 * q], v.e[2 * q + 1]);
+}
+template <int V>
+__device__ __forceinline__ void set_pair(Vf<V>& v, int q, float2 t) {
+  v.e[2 * q] = t.x;
+  v.e[2 * q + 1] = t.y;
+}
+
 // Asynchronous global -> shared copies of base[off ...]; when ok is false nothing is read
 // (base may then be null) and the destination is filled with zeros (src-size 0).
 // fallback is any valid global address.
@@ -343,10 +354,11 @@ __global__ void __launch_bounds__(Width<MODE>::kThreads, Width<MODE>::kMinBlocks
         const V zb = lds_v<kVec>(slot, R::kZB, lane);
         const bool odd = n & 1;
 #pragma unroll
-        for (int jj = 0; jj < kVec; ++jj) zz.e[jj] = odd ? 0.5f * (zz.e[jj] + zb.e[jj]) : zz.e[jj];
+        for (int q = 0; q < kVec / 2; ++q)
+          set_pair(zz, q, odd ? __fmul2_rn(make_float2(0.5f, 0.5f), __fadd2_rn(pair(zz, q), pair(zb, q))) : pair(zz, q));
       }
 #pragma unroll
-      for (int jj = 0; jj < kVec; ++jj) x.e[jj] = fmaf(pm.e[jj], zz.e[jj], x.e[jj]);
+      for (int q = 0; q < kVec / 2; ++q) set_pair(x, q, __ffma2_rn(pair(pm, q), pair(zz, q), pair(x, q)));
     }
     out.v[0] = x;
 #pragma unroll
@@ -377,7 +389,8 @@ __global__ void __launch_bounds__(Width<MODE>::kThreads, Width<MODE>::kMinBlocks
           stage<DIR>(-a.omega, out.v[S], in.v[S], in.hl[S + 1], in.hr[S + 1], out.hl[S + 1], out.hr[S + 1], b, cf);
       V r;
 #pragma unroll
-      for (int jj = 0; jj < kVec; ++jj) r.e[jj] = (DIR ? a.Wo : dw.e[jj]) * y.e[jj];
+      for (int q = 0; q < kVec / 2; ++q)
+        set_pair(r, q, __fmul2_rn(DIR ? make_float2(a.Wo, a.Wo) : pair(dw, q), pair(y, q)));
       out.r = r;
       if (MODE == 5) out.rp = in.r;
       if (MODE == 1) {
@@ -400,15 +413,17 @@ __global__ void __launch_bounds__(Width<MODE>::kThreads, Width<MODE>::kMinBlocks
           // b_c[m] = (r[2m] + r[2m+1]) / 2 (causal P^T with s = 1/2); forward: emitted at
           // row 2m+1 (row NT alone when NT is even); J^T: emitted at row 2m
 #pragma unroll
-          for (int jj = 0; jj < kVec; ++jj) sum.e[jj] = (ADJ || odd) ? r.e[jj] + in.r.e[jj] : r.e[jj];
+          for (int q = 0; q < kVec / 2; ++q)
+            set_pair(sum, q, (ADJ || odd) ? __fadd2_rn(pair(r, q), pair(in.r, q)) : pair(r, q));
           put = ADJ ? (emit && !odd) : (emit && (odd || n == a.NT));
           m = n >> 1;
         } else {
           // b_c[m] = (r[2m] + (r[2m-1] + r[2m+1]) / 2) / 2 (bilinear P^T with s = 1/2),
           // emitted when the last of its three fine rows has been processed
 #pragma unroll
-          for (int jj = 0; jj < kVec; ++jj)
-            sum.e[jj] = odd ? in.r.e[jj] + 0.5f * (in.rp.e[jj] + r.e[jj]) : r.e[jj] + 0.5f * in.r.e[jj];
+          for (int q = 0; q < kVec / 2; ++q)
+            set_pair(sum, q, odd ? __ffma2_rn(make_float2(0.5f, 0.5f), __fadd2_rn(pair(in.rp, q), pair(r, q)), pair(in.r, q))
+                            : __ffma2_rn(make_float2(0.5f, 0.5f), pair(in.r, q), pair(r, q)));
           if (!ADJ) {
             const int nm = n - 1;
             m = odd ? nm >> 1 : n >> 1;
@@ -421,7 +436,9 @@ __global__ void __launch_bounds__(Width<MODE>::kThreads, Width<MODE>::kMinBlocks
         }
         V o;
 #pragma unroll
-        for (int jj = 0; jj < kVec; ++jj) o.e[jj] = 0.5f * (m == 0 ? a.cwW : cwt.e[jj]) * sum.e[jj];
+        for (int q = 0; q < kVec / 2; ++q)
+          set_pair(o, q, __fmul2_rn(__fmul2_rn(make_float2(0.5f, 0.5f), m == 0 ? make_float2(a.cwW, a.cwW) : pair(cwt, q)),
+                               pair(sum, q)));
         if (put && owner) stg_v(a.bc + (size_t)m * a.pc + col, o);
       }
     }
