@@ -26,6 +26,19 @@ inline unsigned blocks_for(long long n, int threads = kThreads) {
   return (unsigned)(b < 1 ? 1 : b);
 }
 
+// Grids of at most kPdlMaxBlocks blocks (the levels below ~300 k DOFs, where a launch costs
+// more than the work) go out with programmatic dependent launch, so that a kernel's launch
+// overlaps its predecessor's drain; each such kernel calls pdl_wait() before any access to
+// memory.  Larger grids launch the ordinary way: launched early, their fixed grids of
+// FP64-bound blocks land unevenly on the SMs (measured slower).
+constexpr unsigned kPdlMaxBlocks = 1216;
+template <typename... KArgs, typename... Args>
+cudaError_t launch_small(void (*kernel)(KArgs...), unsigned blocks, cudaStream_t s, Args... args) {
+  if (blocks <= kPdlMaxBlocks) return launch_pdl(kernel, dim3(blocks), dim3(kThreads), s, args...);
+  kernel<<<blocks, kThreads, 0, s>>>(args...);
+  return cudaGetLastError();
+}
+
 // Row and node of a flat DOF index idx = n (N+1) + i (idx < 2^31).
 __device__ __forceinline__ void split_index(uint32_t idx, const FastDiv& fd, int& n, int& i) {
   const uint32_t q = (uint32_t)(((uint64_t)__umulhi(idx, fd.M) + idx) >> fd.s);
@@ -75,6 +88,7 @@ __device__ __forceinline__ T add_neighbours(const LevelView<T>& lv, const T* __r
 template <typename T, bool ADJ>
 __global__ void __launch_bounds__(kThreads) k_sweep(LevelView<T> lv, uint32_t total, const T* __restrict__ u,
                                                     const T* __restrict__ bs, T* __restrict__ uo) {
+  pdl_wait();  // a no-op unless launched dependent (small grids)
   const uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= total) return;
   int n, i;
@@ -148,6 +162,7 @@ __global__ void __launch_bounds__(kThreads) k_sweep_norm(LevelView<T> lv, uint32
 template <typename T, bool ADJ, int MODE>
 __global__ void __launch_bounds__(kThreads) k_residual(LevelView<T> lv, uint32_t total, const T* __restrict__ u,
                                                        const T* __restrict__ bs, T* __restrict__ r) {
+  pdl_wait();  // a no-op unless launched dependent (small grids)
   const uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= total) return;
   int n, i;
@@ -171,6 +186,7 @@ template <typename T, int TYPE>
 __global__ void __launch_bounds__(kThreads) k_restrict_scaled(int Nf, int NTf, int pf, const T* cf, T r0, T r0h,
                                                               const T* __restrict__ y, LevelView<T> cv,
                                                               uint32_t total, T* __restrict__ bc) {
+  pdl_wait();  // a no-op unless launched dependent (small grids)
   const uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= total) return;
   int m, j;
@@ -277,6 +293,7 @@ __global__ void __launch_bounds__(kThreads) k_restrict(int type, int Nf, int NTf
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_prolong_add(int type, int Nf, int NTf, FastDiv fdc, uint32_t total,
                                                           int pf, T* __restrict__ u, int pc, const T* __restrict__ z) {
+  pdl_wait();  // a no-op unless launched dependent (small grids)
   const uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= total) return;
   int a, c;
@@ -787,8 +804,9 @@ inline uint32_t dofs(const LevelView<T>& lv) {
 template <typename T>
 cudaError_t launch_sweep(const LevelView<T>& lv, bool adj, const T* u, const T* bs, T* uo, cudaStream_t s) {
   const uint32_t n = dofs(lv);
-  if (adj) k_sweep<T, true><<<blocks_for(n), kThreads, 0, s>>>(lv, n, u, bs, uo);
-  else k_sweep<T, false><<<blocks_for(n), kThreads, 0, s>>>(lv, n, u, bs, uo);
+  const cudaError_t e = adj ? launch_small(k_sweep<T, true>, blocks_for(n), s, lv, n, u, bs, uo)
+                            : launch_small(k_sweep<T, false>, blocks_for(n), s, lv, n, u, bs, uo);
+  if (e != cudaSuccess) return e;
   count_launches(1);
   return cudaGetLastError();
 }
@@ -817,8 +835,9 @@ cudaError_t launch_residual(const LevelView<T>& lv, bool adj, const T* u, const 
 template <typename T>
 cudaError_t launch_residual_scaled(const LevelView<T>& lv, bool adj, const T* u, const T* bs, T* y, cudaStream_t s) {
   const uint32_t n = dofs(lv);
-  if (adj) k_residual<T, true, 2><<<blocks_for(n), kThreads, 0, s>>>(lv, n, u, bs, y);
-  else k_residual<T, false, 2><<<blocks_for(n), kThreads, 0, s>>>(lv, n, u, bs, y);
+  const cudaError_t e = adj ? launch_small(k_residual<T, true, 2>, blocks_for(n), s, lv, n, u, bs, y)
+                            : launch_small(k_residual<T, false, 2>, blocks_for(n), s, lv, n, u, bs, y);
+  if (e != cudaSuccess) return e;
   count_launches(1);
   return cudaGetLastError();
 }
@@ -828,10 +847,12 @@ cudaError_t launch_restrict_scaled(int type, int Nf, int NTf, int pf, const T* c
                                    const LevelView<T>& cv, T* bc, cudaStream_t s) {
   const uint32_t n = dofs(cv);
   const T r0h = T(0.5) * r0;
-  if (type == 1) k_restrict_scaled<T, 1><<<blocks_for(n), kThreads, 0, s>>>(Nf, NTf, pf, coef, r0, r0h, y, cv, n, bc);
-  else if (type == 2)
-    k_restrict_scaled<T, 2><<<blocks_for(n), kThreads, 0, s>>>(Nf, NTf, pf, coef, r0, r0h, y, cv, n, bc);
-  else k_restrict_scaled<T, 3><<<blocks_for(n), kThreads, 0, s>>>(Nf, NTf, pf, coef, r0, r0h, y, cv, n, bc);
+  const unsigned g = blocks_for(n);
+  const cudaError_t e =
+      type == 1   ? launch_small(k_restrict_scaled<T, 1>, g, s, Nf, NTf, pf, coef, r0, r0h, y, cv, n, bc)
+      : type == 2 ? launch_small(k_restrict_scaled<T, 2>, g, s, Nf, NTf, pf, coef, r0, r0h, y, cv, n, bc)
+                  : launch_small(k_restrict_scaled<T, 3>, g, s, Nf, NTf, pf, coef, r0, r0h, y, cv, n, bc);
+  if (e != cudaSuccess) return e;
   count_launches(1);
   return cudaGetLastError();
 }
@@ -869,7 +890,8 @@ cudaError_t launch_prolong_add(int type, int Nf, int NTf, int pf, T* u, int Nc, 
   const int width = type == 1 ? Nc + 1 : Nf + 1;
   const int rows = type == 1 ? NTf + 1 : NTc + 1;
   const uint32_t n = (uint32_t)((uint64_t)rows * (uint64_t)width);
-  k_prolong_add<T><<<blocks_for(n), kThreads, 0, s>>>(type, Nf, NTf, make_fastdiv(width), n, pf, u, pc, z);
+  const cudaError_t e = launch_small(k_prolong_add<T>, blocks_for(n), s, type, Nf, NTf, make_fastdiv(width), n, pf, u, pc, z);
+  if (e != cudaSuccess) return e;
   count_launches(1);
   return cudaGetLastError();
 }
