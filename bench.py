@@ -266,9 +266,9 @@ SERVING_OPTS = dict(precision="mixed", tol=TOL, nu=60, max_cycles=300)
 # of the kernel on the named workload; a kernel changed since its capture has no entry.
 NCU_TRAFFIC = {
     ("filtered-simp-4096x16384", "k_sweep<double>"): 1.590e9,
-    ("filtered-simp-4096x16384", "k_defect (FP64, finest level)"): 1.3329e9,
-    ("filtered-simp-4096x16384", "k_stream UP + FP64 accumulate (finest level)"): 1.7467e9,
-    ("filtered-simp-4096x16384", "k_stream DOWN from zero (finest level)"): 0.6300e9,
+    ("filtered-simp-4096x16384", "k_defect (FP64, finest level)"): 1.3325e9,
+    ("filtered-simp-4096x16384", "k_stream UP + FP64 accumulate (finest level)"): 1.7477e9,
+    ("filtered-simp-4096x16384", "k_stream DOWN from zero (finest level)"): 0.6297e9,
 }
 
 
