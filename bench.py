@@ -478,7 +478,7 @@ def main():
         solver.solve(uh, q=qh)
         barrier()
         t1 = time.perf_counter()
-        ksteps = max(1, min(args.steps, 3))
+        ksteps = max(1, min(args.steps, 5))
         for _ in range(ksteps):
             solver.solve(uh, q=qh)
         torch.cuda.synchronize()
