@@ -260,6 +260,7 @@ def workload_opts(w, args=None):
 
 
 SERVING_OPTS = dict(precision="mixed", tol=TOL, nu=60, max_cycles=300)
+SERVING_MAX_NU = 240  # a request that does not converge is solved again with 2x the sweeps, up to this
 
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture
@@ -319,7 +320,7 @@ def run_serving(nreq, workers, inner=3, compare=8):
     reqs = wl.serving_requests()[:nreq]
     fields = lambda r: wl.request_fields(r)[:2]  # noqa: E731
     opts = dict(SERVING_OPTS, mixed_inner_cycles=inner)
-    with sv.Server(workers=workers) as srv:
+    with sv.Server(workers=workers, max_nu=SERVING_MAX_NU) as srv:
         sv.replay(srv, reqs[: min(4, nreq)], fields, speed=1e9, **opts)  # warm-up
         _, closed = sv.replay(srv, reqs, fields, speed=1e9, **opts)
         rate = closed["requests"] / closed["makespan_s"]  # requests per second
@@ -334,11 +335,11 @@ def run_serving(nreq, workers, inner=3, compare=8):
         _, batched = sv.replay(srv, sub, fields, speed=1e9, **opts)
     fp64_opts = dict(opts, precision="fp64")
     fp64_opts.pop("mixed_inner_cycles")
-    with sv.Server(workers=1) as one:
+    with sv.Server(workers=1, max_nu=SERVING_MAX_NU) as one:
         _, single = sv.replay(one, sub, fields, speed=1e9, **fp64_opts)
     vs = {"requests": len(sub), "mixed_batched": batched, "fp64_single": single,
           "speedup": batched["dofs_per_s"] / single["dofs_per_s"] if single["dofs_per_s"] > 0 else None}
-    return {"requests": nreq, "of": 512, "workers": workers, "solver": opts,
+    return {"requests": nreq, "of": 512, "workers": workers, "solver": opts, "max_nu": SERVING_MAX_NU,
             "closed_loop": closed, "poisson_0.8": poisson,
             "p50_p99_by_load": {str(l): [v["p50_s"], v["p99_s"]] for l, v in loads.items()},
             "p50_s": poisson["p50_s"], "p99_s": poisson["p99_s"], "dofs_per_s": closed["dofs_per_s"],

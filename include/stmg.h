@@ -281,7 +281,9 @@ stmg_status stmg_sensitivity_noalloc(int nel, int nt, double L, double t_end, co
  * budget_bytes.  Submitted requests wait in one FIFO queue and start when a worker is free
  * and their footprint (stmg_footprint, plus staging for an element-load array) fits in the
  * budget next to the running requests; several requests run at once and their kernels
- * overlap on the GPU.  Finished hierarchies stay resident in the arena and are reused by
+ * overlap on the GPU.  A request that the arena cannot place next to the others (its free
+ * bytes split into pieces) waits until the running requests finish and runs on the emptied
+ * arena.  Finished hierarchies stay resident in the arena and are reused by
  * later requests with the same grid and options (cache != 0) until memory is needed.  A
  * request's result does not depend on what else runs: it is bit-identical alone and in any
  * mix.  Latencies are measured on the server's steady clock (stmg_server_now). */
@@ -291,6 +293,9 @@ typedef struct {
     int workers;            /* [4] concurrent solves */
     long long budget_bytes; /* [0 = half of the free device memory] arena size */
     int cache;              /* [1] keep finished hierarchies for reuse */
+    int max_nu;             /* [0] > 0: a request that reaches max_cycles or diverges is solved
+                               again with twice the smoothing sweeps, up to max_nu (the decision
+                               depends only on the request, so results stay mix-independent) */
 } stmg_server_opts;
 
 typedef struct {
@@ -315,6 +320,7 @@ typedef struct {
     double t_submit, t_start, t_end;  /* seconds on the server clock */
     long long bytes;        /* device bytes the request's hierarchy held */
     int worker;
+    int nu;                 /* smoothing sweeps of the solve that produced the result */
 } stmg_result;
 
 void stmg_server_default_opts(stmg_server_opts* opts);

@@ -45,7 +45,7 @@ class Opts(C.Structure):
 
 
 class ServerOpts(C.Structure):
-    _fields_ = [("workers", C.c_int), ("budget_bytes", C.c_longlong), ("cache", C.c_int)]
+    _fields_ = [("workers", C.c_int), ("budget_bytes", C.c_longlong), ("cache", C.c_int), ("max_nu", C.c_int)]
 
 
 class Request(C.Structure):
@@ -57,7 +57,7 @@ class Request(C.Structure):
 class Result(C.Structure):
     _fields_ = [("status", C.c_int), ("cycles", C.c_int), ("relres", C.c_double), ("theta", C.c_double),
                 ("t_submit", C.c_double), ("t_start", C.c_double), ("t_end", C.c_double), ("bytes", C.c_longlong),
-                ("worker", C.c_int)]
+                ("worker", C.c_int), ("nu", C.c_int)]
 
 
 _lib = None

@@ -115,6 +115,7 @@ struct Job {
   long long need = 0;
   stmg_result res{};
   bool done = false;
+  bool alone = false;  // the arena could not place it next to others: run it on an emptied arena
 };
 
 struct Idle {
@@ -175,6 +176,20 @@ void worker_main(stmg_server_s* S, int w) {
         if (S->stop && S->queue.empty()) break;
         if (!S->queue.empty()) {
           Job* head = S->queue.front();
+          if (head->alone) {
+            // its free bytes were split into pieces: wait until nothing runs, release the
+            // cached hierarchies, and run it on the emptied arena
+            if (S->running == 0) {
+              while (!S->idle.empty()) destroy_idle(S, S->idle.begin());
+              job = head;
+              S->queue.pop_front();
+              S->inflight += job->need;
+              ++S->running;
+              break;
+            }
+            S->cv_work.wait(lk);
+            continue;
+          }
           // reuse a resident hierarchy of the same grid and options if there is one
           for (auto it = S->idle.begin(); it != S->idle.end(); ++it)
             if (it->key == head->key) {
@@ -226,13 +241,39 @@ void worker_main(stmg_server_s* S, int w) {
       if (!qdev) st = STMG_ENOMEM;
       else if (cudaMemcpyAsync(qdev, job->q, nq, cudaMemcpyDefault, stream) != cudaSuccess) st = STMG_ECUDA;
     }
-    if (st == STMG_OK) {
-      const double scale = job->adjoint ? job->tT / job->nt : 1.0;
+    const double scale = job->adjoint ? job->tT / job->nt : 1.0;
+    if (st == STMG_OK)
       st = stmg_solve_resident(h, job->adjoint != 0, qdev, job->q_value, scale, job->out, &job->res.cycles,
                                &job->res.relres, &job->res.theta);
+    // not converged: again with twice the smoothing sweeps, up to max_nu (a decision that
+    // depends only on this request); the hierarchy is rebuilt with the new options, in the
+    // memory the old one held (the footprint does not depend on nu)
+    while ((st == STMG_EMAXITER || st == STMG_EDIVERGED) && S->o.max_nu > 0 && 2 * job->opts.nu <= S->o.max_nu) {
+      stmg_destroy(h);
+      h = nullptr;
+      job->opts.nu *= 2;
+      job->key = job_key(*job);
+      st = stmg_create_with_allocator(&h, job->nel, job->nt, job->L, job->tT, job->k.data(), job->c.data(),
+                                      &job->opts, stream, arena_alloc, arena_free, &S->arena);
+      if (st == STMG_OK)
+        st = stmg_solve_resident(h, job->adjoint != 0, qdev, job->q_value, scale, job->out, &job->res.cycles,
+                                 &job->res.relres, &job->res.theta);
     }
     if (qdev) S->arena.release(qdev);
+    if (st == STMG_ENOMEM && !job->alone) {
+      // the free bytes did not hold it in one piece next to the others: back to the head of
+      // the queue, to run once the running requests are done
+      if (h) stmg_destroy(h);
+      std::lock_guard<std::mutex> lk(S->mu);
+      --S->running;
+      S->inflight -= job->need;
+      job->alone = true;
+      S->queue.push_front(job);
+      S->cv_work.notify_all();
+      continue;
+    }
     job->res.status = st;
+    job->res.nu = job->opts.nu;
     job->res.bytes = h ? stmg_device_bytes(h) : 0;
     job->res.t_end = S->now();
     {
@@ -264,6 +305,7 @@ void stmg_server_default_opts(stmg_server_opts* o) {
   o->workers = 4;
   o->budget_bytes = 0;
   o->cache = 1;
+  o->max_nu = 0;
 }
 
 stmg_status stmg_server_create(stmg_server_t* out, const stmg_server_opts* opts) {

@@ -23,11 +23,14 @@ def _lib():
 
 
 class Server:
-    def __init__(self, workers=4, budget_bytes=0, cache=True):
+    def __init__(self, workers=4, budget_bytes=0, cache=True, max_nu=0):
+        """max_nu > 0: a request that reaches its cycle cap or diverges is solved again with
+        twice the smoothing sweeps, up to max_nu."""
         L = _lib()
         o = ServerOpts()
         L.stmg_server_default_opts(C.byref(o))
         o.workers, o.budget_bytes, o.cache = int(workers), int(budget_bytes), int(bool(cache))
+        o.max_nu = int(max_nu)
         h = C.c_void_p()
         B.check(L.stmg_server_create(C.byref(h), C.byref(o)))
         self._h = h
@@ -51,7 +54,7 @@ class Server:
         if r.status >= 0:
             self._keep.pop(ticket, None)
         return dict(status=B.STATUS.get(r.status, "pending"), cycles=r.cycles, relres=r.relres, theta=r.theta,
-                    t_submit=r.t_submit, t_start=r.t_start, t_end=r.t_end, bytes=r.bytes, worker=r.worker)
+                    t_submit=r.t_submit, t_start=r.t_start, t_end=r.t_end, bytes=r.bytes, worker=r.worker, nu=r.nu)
 
     def drain(self):
         B.check(_lib().stmg_server_drain(self._h))
@@ -104,7 +107,9 @@ def replay(server, requests, fields, speed=1.0, **opts):
     lat = np.array([x["t_end"] - x["t_submit"] for x in res])
     dofs = np.array([(r["N"] + 1) * (r["NT"] + 1) for r in requests], dtype=np.float64)
     span = max(x["t_end"] for x in res) - min(x["t_submit"] for x in res)
+    nu0 = opts.get("nu")
     summary = dict(requests=len(res), ok=sum(x["status"] == "ok" for x in res),
+                   nu_raised=sum(1 for x in res if nu0 and x["nu"] > nu0),
                    p50_s=float(np.percentile(lat, 50)), p99_s=float(np.percentile(lat, 99)),
                    dofs_per_s=float(dofs.sum() / span), makespan_s=float(span),
                    mean_cycles=float(np.mean([x["cycles"] for x in res])), peak_bytes=int(server.peak_bytes))

@@ -84,3 +84,27 @@ def test_admission_respects_budget_and_refuses_oversize():
     big = dict(reqs[0], N=4096, NT=4096)
     outs, res, _ = _run([reqs[1], big, reqs[2]], workers=2, budget=budget, cache=False)
     assert [x["status"] for x in res] == ["ok", "enomem", "ok"]
+
+
+def test_smoothing_escalation_is_per_request():
+    """With max_nu, a request that reaches its cycle cap or diverges is solved again with
+    twice the sweeps, up to max_nu; the result states the sweeps used and equals the same
+    request served alone with those sweeps from the start (the decision depends only on the
+    request itself)."""
+    reqs = _reqs(6, seed=11)
+    opts = dict(OPTS, nu=2, max_cycles=30)
+    max_nu = 128
+    outs = [np.full((r["NT"] + 1, r["N"] + 1), np.nan) for r in reqs]
+    with sv.Server(workers=3, max_nu=max_nu) as s:
+        ts = [s.submit(r["N"], r["NT"], r["L"], r["tT"], *wl.request_fields(r)[:2], q_value=1.0,
+                       adjoint=r["adjoint"], out=o, **opts) for r, o in zip(reqs, outs)]
+        res = [s.result(t) for t in ts]
+    assert any(x["nu"] > 2 for x in res)  # the cap really forced escalations
+    for r, o, x in zip(reqs, outs, res):
+        assert x["status"] == "ok" or x["nu"] == max_nu
+        one = np.full_like(o, np.nan)
+        with sv.Server(workers=1, cache=False) as s1:
+            y = s1.result(s1.submit(r["N"], r["NT"], r["L"], r["tT"], *wl.request_fields(r)[:2], q_value=1.0,
+                                    adjoint=r["adjoint"], out=one, **dict(opts, nu=x["nu"])))
+        assert (y["status"], y["nu"], y["cycles"]) == (x["status"], x["nu"], x["cycles"])
+        assert np.array_equal(o, one, equal_nan=True)
