@@ -44,3 +44,32 @@ def test_default_opts_and_errors_without_gpu():
     with pytest.raises(_binding.STMGError):
         _binding.make_opts(no_such_option=1)
     assert _binding.STATUS[lib.stmg_mixed_pass(None, 0, 0, 0)] == "einval"
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The ctypes mirrors of the header's structs (options, server options, request,
+    result) have the C compiler's size and field offsets, field by field and by name."""
+    import shutil
+    import subprocess
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    pairs = [("stmg_opts", _binding.Opts), ("stmg_server_opts", _binding.ServerOpts),
+             ("stmg_request", _binding.Request), ("stmg_result", _binding.Result)]
+    lines = ['#include "stmg.h"', "#include <stddef.h>", "#include <stdio.h>", "int main(void) {"]
+    expect = []
+    for cname, cls in pairs:
+        lines.append('  printf("%%zu\\n", sizeof(%s));' % cname)
+        expect.append(ctypes.sizeof(cls))
+        for fname, _ in cls._fields_:
+            lines.append('  printf("%%zu\\n", offsetof(%s, %s));' % (cname, fname))
+            expect.append(getattr(cls, fname).offset)
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    inc = os.path.join(ROOT, "include")
+    subprocess.run([cc, "-std=c99", "-I", inc, str(src), "-o", str(exe)], check=True, capture_output=True)
+    got = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+    assert got == expect
