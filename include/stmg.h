@@ -260,18 +260,21 @@ stmg_status stmg_mixed_pass(stmg_t handle, int level, int adjoint, int kind);
  * Same result as stmg_sensitivity, without a handle and without any allocation:
  * nel, nt, L, t_end describe the grid as in stmg_create; chi (nel), u and lam
  * ((nt+1) x (nel+1), dense rows) and dtheta_dchi (nel) must all be device memory of the
- * current device (host arrays are rejected with STMG_EINVAL, since staging them would
- * need an allocation); simp6 is a host array as in stmg_simp; stream may be NULL.
+ * current device or managed memory (host arrays, and device arrays of another GPU, are
+ * rejected with STMG_EINVAL: staging them would need an allocation); simp6 is a host
+ * array as in stmg_simp; stream may be NULL.
  * The partial sums live in one fixed array of STMG_NOALLOC_MAX_SCRATCH doubles (8 MiB)
  * inside the library's device image, which every GPU that loads the library keeps until
- * the process exits.  The call needs 2 * ceil((nt+1)/256) * nel of them and rejects
- * larger problems with STMG_EINVAL (for example nel = 4096 with nt up to 32767).
+ * the process exits.  The call needs 2 * (floor(nt/256) + 1) * nel of them and rejects
+ * larger problems with STMG_EINVAL (for example nel = 4096 with nt up to 32767); it also
+ * rejects nt >= 65535 * 256, whose time chunks exceed one launch's grid.
  * The first call on each device looks up that array's device address; make it before
  * any stream capture.  All calls share the array: calls whose work overlaps on the GPU
  * (different streams or host threads without ordering) race and give wrong results, so
  * serialise them.  Every scratch value read is written earlier in the same call, so a
- * previous call's contents never leak into a result.  Returns after dtheta_dchi is
- * complete; messages go to stmg_last_error(NULL). */
+ * previous call's contents never leak into a result.  The call synchronises its stream
+ * (cudaStreamSynchronize) and returns after dtheta_dchi is complete; messages go to
+ * stmg_last_error(NULL). */
 #define STMG_NOALLOC_MAX_SCRATCH (1 << 20)
 stmg_status stmg_sensitivity_noalloc(int nel, int nt, double L, double t_end, const double* chi, const double* simp6,
                                      const double* u, const double* lam, double* dtheta_dchi, void* stream);

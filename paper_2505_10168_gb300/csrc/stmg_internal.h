@@ -290,7 +290,10 @@ cudaError_t launch_sensitivity(int N, int NT, int pitch, double dx, double dt, c
 // Per-element reduction of scratch[2 * chunks * N] partial sums into the gradient.
 cudaError_t launch_sens_final(int N, int chunks, const double* chi, Simp6 sp, const double* scratch, double* g,
                               cudaStream_t s);
-// Time levels 0..NT in chunks of kSensRowsPerChunk rows.
+// Largest gridDim.y (and z) of a launch.
+constexpr int kMaxGridY = 65535;
+// Time levels 0..NT in chunks of kSensRowsPerChunk rows (the chunks are gridDim.y of the
+// partial-sum launch).
 inline int sens_chunks(int NT) { return (NT + kSensRowsPerChunk) / kSensRowsPerChunk; }
 
 }  // namespace stmg

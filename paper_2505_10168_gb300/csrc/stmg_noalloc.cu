@@ -15,6 +15,7 @@
 
 #include "stmg.h"
 #include "stmg_internal.h"
+#include "stmg_placement.h"
 
 namespace stmg {
 namespace {
@@ -51,13 +52,15 @@ stmg_status scratch_address(double** out) {
   return STMG_OK;
 }
 
-bool on_device(const void* p) {
+// Where a pointer lives relative to the current device (kPlaceUsable, kPlaceOtherDevice
+// or kPlaceNotDevice; an unknown pointer counts as host memory).
+int placement(const void* p, int current_device) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
-    return false;
+    return kPlaceNotDevice;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  return noalloc_placement(static_cast<int>(a.type), a.device, current_device);
 }
 
 }  // namespace
@@ -68,8 +71,8 @@ using namespace stmg;
 extern "C" stmg_status stmg_sensitivity_noalloc(int nel, int nt, double L, double t_end, const double* chi,
                                                 const double* simp6, const double* u, const double* lam,
                                                 double* dtheta_dchi, void* stream) {
-  if (nel < 1 || nt < 1 || !(L > 0.0) || !(t_end > 0.0) || !chi || !simp6 || !u || !lam || !dtheta_dchi) {
-    set_global_error("stmg_sensitivity_noalloc: need nel >= 1, nt >= 1, L > 0, t_end > 0 and non-NULL arrays");
+  if (nel < 1 || nt < 1 || nt > (1 << 30) || !(L > 0.0) || !(t_end > 0.0) || !chi || !simp6 || !u || !lam || !dtheta_dchi) {
+    set_global_error("stmg_sensitivity_noalloc: need nel >= 1, 1 <= nt <= 2^30, L > 0, t_end > 0 and non-NULL arrays");
     return STMG_EINVAL;
   }
   const long long need = 2LL * sens_chunks(nt) * nel;
@@ -81,9 +84,32 @@ extern "C" stmg_status stmg_sensitivity_noalloc(int nel, int nt, double L, doubl
     set_global_error(buf);
     return STMG_EINVAL;
   }
-  if (!on_device(chi) || !on_device(u) || !on_device(lam) || !on_device(dtheta_dchi)) {
-    set_global_error("stmg_sensitivity_noalloc: chi, u, lam and dtheta_dchi must be device memory");
+  if (sens_chunks(nt) > kMaxGridY) {
+    char buf[256];
+    snprintf(buf, sizeof buf,
+             "stmg_sensitivity_noalloc: nt=%d gives %d time chunks of %d rows, more than the %d a launch can hold",
+             nt, sens_chunks(nt), kSensRowsPerChunk, kMaxGridY);
+    set_global_error(buf);
     return STMG_EINVAL;
+  }
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    set_global_error("stmg_sensitivity_noalloc: no usable current device");
+    return STMG_ECUDA;
+  }
+  const void* arrays[4] = {chi, u, lam, dtheta_dchi};
+  for (const void* a : arrays) {
+    const int where = placement(a, dev);
+    if (where == kPlaceOtherDevice) {
+      set_global_error("stmg_sensitivity_noalloc: chi, u, lam and dtheta_dchi must be on the current device, "
+                       "not on another GPU");
+      return STMG_EINVAL;
+    }
+    if (where != kPlaceUsable) {
+      set_global_error("stmg_sensitivity_noalloc: chi, u, lam and dtheta_dchi must be device memory");
+      return STMG_EINVAL;
+    }
   }
   double* scratch = nullptr;
   stmg_status st = scratch_address(&scratch);

@@ -73,3 +73,42 @@ def test_struct_layouts_match_the_header(tmp_path):
     subprocess.run([cc, "-std=c99", "-I", inc, str(src), "-o", str(exe)], check=True, capture_output=True)
     got = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
     assert got == expect
+
+
+def test_noalloc_placement_rule(tmp_path):
+    """stmg_sensitivity_noalloc takes device memory of the current device or managed
+    memory, and refuses host memory and device memory of another GPU (which the current
+    device cannot read without peer access).  The rule is checked here on the host,
+    against the CUDA runtime's own cudaMemoryType values, without any device."""
+    import shutil
+    import subprocess
+
+    cxx = shutil.which("g++") or shutil.which("c++")
+    cuda_inc = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "include")
+    if cxx is None or not os.path.exists(os.path.join(cuda_inc, "driver_types.h")):
+        pytest.skip("no C++ compiler or CUDA headers")
+    src = tmp_path / "placement.cc"
+    src.write_text("\n".join([
+        "#include <cstdio>",
+        "#include <driver_types.h>",
+        '#include "stmg_placement.h"',
+        "using namespace stmg;",
+        "int main() {",
+        "  int bad = 0;",
+        "  bad += noalloc_placement(cudaMemoryTypeDevice, 0, 0) != kPlaceUsable;",
+        "  bad += noalloc_placement(cudaMemoryTypeDevice, 3, 3) != kPlaceUsable;",
+        "  bad += noalloc_placement(cudaMemoryTypeDevice, 1, 0) != kPlaceOtherDevice;",
+        "  bad += noalloc_placement(cudaMemoryTypeDevice, 0, 2) != kPlaceOtherDevice;",
+        "  bad += noalloc_placement(cudaMemoryTypeManaged, 1, 0) != kPlaceUsable;",
+        "  bad += noalloc_placement(cudaMemoryTypeHost, 0, 0) != kPlaceNotDevice;",
+        "  bad += noalloc_placement(cudaMemoryTypeUnregistered, 0, 0) != kPlaceNotDevice;",
+        '  std::printf("%d\\n", bad);',
+        "  return 0;",
+        "}",
+    ]) + "\n")
+    exe = tmp_path / "placement"
+    csrc = os.path.join(ROOT, "paper_2505_10168_gb300", "csrc")
+    subprocess.run([cxx, "-std=c++17", "-I", csrc, "-I", cuda_inc, str(src), "-o", str(exe)], check=True,
+                   capture_output=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
+    assert out == ["0"]

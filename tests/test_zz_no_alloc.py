@@ -4,7 +4,8 @@ stmg_sensitivity_noalloc exists for callers that cannot allocate device memory w
 they need a gradient (allocation can synchronise the whole device, or their memory is
 fixed up front).  It keeps its scratch in a fixed array inside the library, so this
 test calls it twice in a row with different inputs and checks each result against
-stmg_sensitivity, and checks that oversize problems and host arrays are refused.
+stmg_sensitivity (and the first also against the CPU oracle), and checks that oversize
+problems and host arrays are refused.
 This file is collected last so that a run stopping at the first failure has already
 run every other test.
 """
@@ -14,6 +15,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 import paper_2505_10168_gb300 as pkg
 from paper_2505_10168_gb300 import _binding as B
 from paper_2505_10168_gb300 import workloads as wl
@@ -49,6 +51,9 @@ def test_noalloc_sensitivity_matches_stmg_sensitivity_twice():
         torch.cuda.synchronize()
         err = (out - ref).abs().max().item() / ref.abs().max().item()
         assert err < 1e-12, (call, err)
+        if call == 0:  # and once against the CPU oracle's sensitivity, independently of the GPU
+            go = oracle.sensitivity(N, NT, L, tT, chi.cpu().numpy(), s6, u.cpu().numpy(), lam.cpu().numpy())
+            assert np.abs(out.cpu().numpy() - go).max() / np.abs(go).max() < 1e-12
     ref_solver.close()
 
 
@@ -62,6 +67,12 @@ def test_noalloc_rejects_oversize_and_host_arrays():
     st = _noalloc(N, NT, 1.0, 1.0, chi, s6, small, small, g)
     assert B.STATUS[st] == "einval"
     assert b"maximum" in B.lib().stmg_last_error(None)
+    # a single element over more time steps than one launch's grid holds in time chunks
+    # (65536 chunks of 256 rows): refused on the host, before any array is touched
+    one = torch.zeros(1, dtype=torch.float64, device=DEV)
+    st = _noalloc(1, 65535 * 256, 1.0, 1.0, one, s6, small, small, one)
+    assert B.STATUS[st] == "einval"
+    assert b"time chunks" in B.lib().stmg_last_error(None)
     n, nt = 8, 8
     chi_h = np.full(n, 0.5)
     u_h = np.zeros((nt + 1, n + 1))
