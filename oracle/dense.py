@@ -102,34 +102,53 @@ def prolongation(N, NT, kind, interp="C"):
     return np.kron(p1d_t(NT, interp), np.eye(N + 1)), 0.5
 
 
-def coarse_material(k, c, kind, reassembly):
+def simp_material(chi, simp6):
+    """SIMP interpolation of Sec. 2.1 for design values chi (vectorised)."""
+    k_ins, k_con, c_ins, c_con, p_k, p_c = [float(v) for v in simp6]
+    chi = np.asarray(chi, dtype=np.float64)
+    return k_ins + (k_con - k_ins) * chi ** p_k, c_ins + (c_con - c_ins) * chi ** p_c
+
+
+def coarse_material(k, c, kind, reassembly, chi=None, simp6=None):
+    """Coarse k, c (and the coarse design field, with D) of one coarsening step: t keeps
+    the material (and chi); x merges element pairs by conductivity (K), resistivity (R)
+    or design-field (D: mean chi of the pair, SIMP re-applied) averaging (Sec. 3.1, 5.1).
+    Returns (k, c, chi)."""
     if kind == "t":
-        return k.copy(), c.copy()
+        return k.copy(), c.copy(), (None if chi is None else chi.copy())
+    if reassembly == "D":
+        chi_c = 0.5 * (chi[0::2] + chi[1::2])
+        kc, cc = simp_material(chi_c, simp6)
+        return kc, cc, chi_c
     k0, k1 = k[0::2], k[1::2]
     c2 = (c[0::2] + c[1::2]) / 2.0
     if reassembly == "R":
-        return 2.0 * k0 * k1 / (k0 + k1), c2
-    return (k0 + k1) / 2.0, c2
+        return 2.0 * k0 * k1 / (k0 + k1), c2, None
+    return (k0 + k1) / 2.0, c2, None
 
 
 class DenseHierarchy:
     """Dense levels for a given coarsening path (string of 'x'/'t').
 
-    reassembly "K" / "R": every level is the all-at-once J of its own grid and averaged
-    material (Sec. 3.1, 5.1); "P": every coarse J is the Galerkin product R J P of the
-    level above (Sec. 5.1)."""
+    reassembly "K" / "R" / "D": every level is the all-at-once J of its own grid and
+    averaged material (Sec. 3.1, 5.1; "D" needs the design field chi and simp6, and the
+    level-0 material is SIMP of chi); "P": every coarse J is the Galerkin product R J P
+    of the level above (Sec. 5.1)."""
 
-    def __init__(self, N, NT, L, tT, k, c, path, interp="C", reassembly="R"):
+    def __init__(self, N, NT, L, tT, k, c, path, interp="C", reassembly="R", chi=None, simp6=None):
         self.levels = []
+        if reassembly == "D":
+            chi = np.asarray(chi, float)
+            k, c = simp_material(chi, simp6)
         k, c = np.asarray(k, float), np.asarray(c, float)
         J = all_at_once(N, NT, L, tT, k, c)
         for l in range(len(path) + 1):
-            lv = dict(N=N, NT=NT, J=J, D=np.diag(J).copy(), k=k, c=c)
+            lv = dict(N=N, NT=NT, J=J, D=np.diag(J).copy(), k=k, c=c, chi=chi)
             if l < len(path):
                 kind = path[l]
                 P, s = prolongation(N, NT, kind, interp)
                 lv["P"], lv["R"] = P, s * P.T
-                k, c = coarse_material(k, c, kind, "K" if reassembly == "P" else reassembly)
+                k, c, chi = coarse_material(k, c, kind, "K" if reassembly == "P" else reassembly, chi, simp6)
                 if kind == "x":
                     N //= 2
                 else:

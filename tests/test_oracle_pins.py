@@ -192,18 +192,125 @@ def test_design_dependent_vs_fixed_deff():
 
 # ---------------------------------------------------------------- transfer operators (Sec. 3.1)
 
-@pytest.mark.parametrize("kind", ["x", "t"])
-def test_prolong_restrict_match_kronecker(kind):
+@pytest.mark.parametrize("kind,interp", [("x", "C"), ("t", "C"), ("x", "B"), ("t", "B")])
+def test_prolong_restrict_match_kronecker(kind, interp):
     N, NT = 8, 8
     k, c = _rand_material(4, N)
     lc = 1e300 if kind == "t" else 0.0
-    H = oracle.Hierarchy(N, NT, 1.0, 1.0, k, c, num_levels=2, lambda_crit=lc)
+    H = oracle.Hierarchy(N, NT, 1.0, 1.0, k, c, num_levels=2, lambda_crit=lc, interp=interp)
     assert H.path() == kind
-    P, s = dense.prolongation(N, NT, kind)
+    P, s = dense.prolongation(N, NT, kind, interp)
     z = _rand_vec(8, H.shape(1))
     u = _rand_vec(9, H.shape(0))
     np.testing.assert_allclose(H.prolong_add(0, z, u).ravel(), u.ravel() + P @ z.ravel(), rtol=1e-15, atol=1e-15)
     np.testing.assert_allclose(H.restrict(0, u).ravel(), s * P.T @ u.ravel(), rtol=1e-15, atol=1e-15)
+
+
+@pytest.mark.parametrize("interp", ["C", "B"])
+def test_time_prolongation_reproduces_polynomials(interp):
+    """Sec. 3.1 / 5.1: the causal t-prolongation copies a coarse value to the fine levels
+    2m and 2m+1 (it reproduces functions constant in time), the bilinear one interpolates
+    linearly between t_2m and t_2m+2 (it reproduces every function linear in t).  The
+    restriction is R = 1/2 P^T, so <R r, z> = 1/2 <r, P z> for all r, z."""
+    N, NT, tT = 6, 16, 2.0
+    k, c = _rand_material(5, N)
+    H = oracle.Hierarchy(N, NT, 1.0, tT, k, c, num_levels=2, lambda_crit=1e300, interp=interp)
+    assert H.path() == "t"
+    tc = np.arange(NT // 2 + 1) * (2.0 * tT / NT)
+    tf = np.arange(NT + 1) * (tT / NT)
+    a, b = wl.uniform(61, N + 1), wl.uniform(62, N + 1) - 0.5
+    zc = a[None, :] + 0.0 * tc[:, None]
+    np.testing.assert_allclose(H.prolong_add(0, zc, np.zeros((NT + 1, N + 1))), a[None, :] + 0.0 * tf[:, None],
+                               rtol=1e-15, atol=0)
+    zl = a[None, :] + b[None, :] * tc[:, None]
+    fine = H.prolong_add(0, zl, np.zeros((NT + 1, N + 1)))
+    lin = a[None, :] + b[None, :] * tf[:, None]
+    if interp == "B":
+        np.testing.assert_allclose(fine, lin, rtol=1e-14, atol=1e-15)
+    else:  # causal: fine row 2m+1 holds the value of t_2m, one fine step behind
+        np.testing.assert_allclose(fine[0::2], lin[0::2], rtol=1e-14, atol=1e-15)
+        np.testing.assert_allclose(fine[1::2], lin[0:-1:2], rtol=1e-14, atol=1e-15)
+    r = _rand_vec(63, H.shape(0))
+    z = _rand_vec(64, H.shape(1))
+    lhs = np.sum(H.restrict(0, r) * z)
+    rhs = 0.5 * np.sum(r * H.prolong_add(0, z, np.zeros(H.shape(0))))
+    assert lhs == pytest.approx(rhs, rel=1e-13)
+
+
+def test_bilinear_t_restriction_by_hand():
+    """Sec. 5.1 bilinear t-restriction on one column: b_c[m] = 1/2 (r[2m] + 1/2 r[2m-1] +
+    1/2 r[2m+1]), the missing rows -1 and NT+1 dropped."""
+    N, NT = 2, 8
+    H = oracle.Hierarchy(N, NT, 1.0, 1.0, np.ones(N), np.ones(N), num_levels=2, lambda_crit=1e300, interp="B")
+    r = np.zeros((NT + 1, N + 1))
+    r[:, 1] = np.arange(1.0, NT + 2.0)  # r[n] = n + 1
+    got = H.restrict(0, r)[:, 1]
+    expect = [0.5 * (1.0 + 0.5 * 2.0), 0.5 * (3.0 + 0.5 * 2.0 + 0.5 * 4.0), 0.5 * (5.0 + 0.5 * 4.0 + 0.5 * 6.0),
+              0.5 * (7.0 + 0.5 * 6.0 + 0.5 * 8.0), 0.5 * (9.0 + 0.5 * 8.0)]
+    np.testing.assert_allclose(got, expect, rtol=1e-15)
+
+
+# ---------------------------------------------------------------- SIMP material model (Sec. 2.1)
+
+def test_simp_hand_values():
+    """k = k_ins + (k_con - k_ins) chi^p_k, c = c_ins + (c_con - c_ins) chi^p_c at points
+    worked out by hand, with p_k != p_c so that a swapped exponent fails."""
+    s6 = [1e-3, 1.0, 0.2, 1.5, 3.0, 2.0]
+    chi = np.array([0.0, 0.25, 0.5, 1.0])
+    k, c = oracle.simp(chi, s6)
+    # chi^3 = 0, 1/64, 1/8, 1; chi^2 = 0, 1/16, 1/4, 1; k_con - k_ins = 0.999, c_con - c_ins = 1.3
+    np.testing.assert_allclose(k, [1e-3, 0.016609375, 0.125875, 1.0], rtol=1e-15)
+    np.testing.assert_allclose(c, [0.2, 0.28125, 0.525, 1.5], rtol=1e-15)
+    k2, c2 = oracle.simp(np.array([0.5]), [2.0, 10.0, 3.0, 7.0, 1.0, 4.0])  # p_k = 1: linear in chi
+    assert k2[0] == pytest.approx(6.0, rel=1e-15) and c2[0] == pytest.approx(3.25, rel=1e-15)
+
+
+# ---------------------------------------------------------------- D-reassembly (Sec. 5.1)
+
+def test_design_reassembly_levels_match_dense():
+    """D-reassembly: on x-coarsening the coarse design value is the mean of the pair and
+    the SIMP model is re-applied; t-coarsening keeps chi.  Level by level against the dense
+    brute force, and by hand on one pair: chi = (0.2, 0.6) gives simp(0.4), which differs
+    from both the arithmetic (K) and the harmonic (R) mean of the pair's k."""
+    N, NT = 16, 16
+    chi = 0.05 + 0.9 * wl.uniform(71, N)
+    chi[0], chi[1] = 0.2, 0.6
+    s6 = [1e-4, 1.0, 0.3, 1.0, 3.0, 2.0]
+    k, c = oracle.simp(chi, s6)
+    H = oracle.Hierarchy(N, NT, 1.0, 0.05, k, c, chi=chi, simp6=s6, reassembly="D", max_coarse_dofs=10)
+    path = H.path()
+    assert "x" in path and "t" in path
+    D = dense.DenseHierarchy(N, NT, 1.0, 0.05, k, c, path, reassembly="D", chi=chi, simp6=s6)
+    for l, lv in enumerate(D.levels):
+        np.testing.assert_allclose(H.levels[l]["k"], lv["k"], rtol=1e-14)
+        np.testing.assert_allclose(H.levels[l]["c"], lv["c"], rtol=1e-14)
+    first_x = path.index("x") + 1
+    k04 = 1e-4 + (1.0 - 1e-4) * 0.4 ** 3
+    assert H.levels[first_x]["k"][0] == pytest.approx(k04, rel=1e-14)
+    assert H.levels[first_x]["c"][0] == pytest.approx(0.3 + 0.7 * 0.16, rel=1e-14)
+    ka, kh = (k[0] + k[1]) / 2, 2 * k[0] * k[1] / (k[0] + k[1])
+    assert abs(k04 - ka) > 0.01 * k04 and abs(k04 - kh) > 0.01 * k04
+
+
+@pytest.mark.parametrize("adj", [False, True])
+def test_design_reassembly_vcycle_matches_dense(adj):
+    N, NT = 16, 16
+    chi = 0.05 + 0.9 * wl.uniform(72, N)
+    s6 = [1e-3, 1.0, 0.5, 1.0, 3.0, 1.0]
+    k, c = oracle.simp(chi, s6)
+    deff = np.sqrt((k / c).min() * (k / c).max())
+    tT = 0.5 * (1.0 / N) ** 2 / deff * NT
+    H = oracle.Hierarchy(N, NT, 1.0, tT, k, c, chi=chi, simp6=s6, reassembly="D", max_coarse_dofs=20, nu=3)
+    path = H.path()
+    assert len(path) >= 2 and "x" in path
+    D = dense.DenseHierarchy(N, NT, 1.0, tT, k, c, path, reassembly="D", chi=chi, simp6=s6)
+    b = _rand_vec(33, H.shape(0))
+    u = np.zeros(H.shape(0))
+    ud = u.ravel().copy()
+    for cyc in range(3):
+        u = H.vcycle(u, b, adj=adj)
+        ud = D.vcycle(0, ud, b.ravel(), nu=3, adj=adj)
+        np.testing.assert_allclose(u.ravel(), ud, rtol=0, atol=1e-12 * np.abs(ud).max())
 
 
 # ---------------------------------------------------------------- V-cycle (Alg. 1) vs dense brute force
@@ -211,14 +318,15 @@ def test_prolong_restrict_match_kronecker(kind):
 @pytest.mark.parametrize("N,NT,lam", [(8, 8, 2.0), (16, 8, 0.05), (8, 16, 0.3), (16, 16, 1.0)])
 @pytest.mark.parametrize("reasm", ["R", "K"])
 @pytest.mark.parametrize("adj", [False, True])
-def test_vcycle_matches_dense_bruteforce(N, NT, lam, reasm, adj):
+@pytest.mark.parametrize("interp", ["C", "B"])
+def test_vcycle_matches_dense_bruteforce(N, NT, lam, reasm, adj, interp):
     k, c = _rand_material(N + NT, N, contrast=1e3)
     deff = np.sqrt((k / c).min() * (k / c).max())
     tT = lam * (1.0 / N) ** 2 / deff * NT
-    H = oracle.Hierarchy(N, NT, 1.0, tT, k, c, reassembly=reasm, max_coarse_dofs=20, nu=3)
+    H = oracle.Hierarchy(N, NT, 1.0, tT, k, c, reassembly=reasm, max_coarse_dofs=20, nu=3, interp=interp)
     path = H.path()
     assert len(path) >= 2
-    D = dense.DenseHierarchy(N, NT, 1.0, tT, k, c, path, reassembly=reasm)
+    D = dense.DenseHierarchy(N, NT, 1.0, tT, k, c, path, reassembly=reasm, interp=interp)
     b = _rand_vec(31, H.shape(0))
     u = np.zeros(H.shape(0))
     ud = u.ravel().copy()
