@@ -50,8 +50,9 @@ def parse():
     p.add_argument("--mixed-inner", type=int, default=3, help="FP32 V-cycles per FP64 defect in the mixed scheme")
     p.add_argument("--mixed-first", type=int, default=3, help="FP32 V-cycles on the first defect in the mixed scheme")
     p.add_argument("--max-coarse-dofs", type=int, default=0, help="planner: stop at a level this small (0: default)")
-    p.add_argument("--serving-requests", type=int, default=64,
+    p.add_argument("--serving-requests", type=int, default=512,
                    help="requests of the 512-request serving trace to replay (0: skip serving)")
+    p.add_argument("--no-all-cores", action="store_true", help="skip the all-cores oracle timing")
     p.add_argument("--serving-workers", type=int, default=6)
     return p.parse_args()
 
@@ -62,7 +63,9 @@ WORKLOADS = ("rod_blocks", "filtered_simp", "filtered_simp_high_contrast", "rand
 def load_workload(name):
     from paper_2505_10168_gb300 import workloads as wl
 
-    return getattr(wl, name)()
+    w = getattr(wl, name)()
+    w["fn"] = name
+    return w
 
 
 def measured_peaks():
@@ -158,6 +161,56 @@ def oracle_sample(w, nt_sample, tol=TOL):
     return dict(value=dofs / dt, seconds=dt, dofs=dofs, cycles=cyc, status=st, relres=float(hist[-1]))
 
 
+def _oracle_sample_task(args):
+    """One oracle sample in a worker process (spawned: the parent holds a CUDA context)."""
+    import importlib
+
+    name, nt_sample = args
+    sys.path.insert(0, ROOT)
+    w = importlib.import_module("paper_2505_10168_gb300.workloads")
+    return oracle_sample(getattr(w, name)(), nt_sample)
+
+
+def cpu_model():
+    """The host CPU's model name and core count (lscpu, else /proc/cpuinfo)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.split(":")[0].strip() in ("Model name", "Model Name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if model is None:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for ln in f:
+                    if ln.lower().startswith("model name"):
+                        model = ln.split(":", 1)[1].strip()
+                        break
+        except Exception:
+            pass
+    return {"model": model, "nproc": os.cpu_count()}
+
+
+def oracle_all_cores(wname, nt_sample, procs=None):
+    """The same oracle sample solved by one process per host core at once (the oracle is
+    serial C; the cores work on independent copies): aggregate DOF/s = procs x DOFs / wall."""
+    import multiprocessing as mp
+
+    procs = procs or os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(procs) as pool:
+        pool.map(_oracle_sample_task, [(wname, 16)] * procs)  # start-up and imports, untimed
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_sample_task, [(wname, nt_sample)] * procs)
+        wall = time.perf_counter() - t0
+    dofs = sum(r["dofs"] for r in res)
+    return {"value": dofs / wall, "unit": "DOF/s", "cores": procs, "seconds": wall,
+            "what": "%d concurrent oracle STMG processes, each solving the same %d-step sample" % (procs, nt_sample)}
+
+
 def oracle_time_stepping(w):
     """Exact sequential implicit time stepping (the oracle's direct solver) on the full grid."""
     import oracle
@@ -174,25 +227,37 @@ def oracle_time_stepping(w):
     return dict(value=(N + 1) * (NT + 1) / dt, seconds=dt, u=u)
 
 
-def cpu_baseline_obj(w, nt_sample=256, solutions=None):
+def accuracy_against_exact(w, solutions):
+    """max |u - u_exact| / max |u_exact| of each host solution of workload w against the
+    oracle's exact time stepping on the full grid."""
+    ts = oracle_time_stepping(w)
+    ue = ts["u"]
+    scale = float(np.abs(ue).max())
+    acc = {name: float(np.abs(v - ue).max() / scale) for name, v in solutions.items()}
+    acc["what"] = "max |u - u_exact| / max |u_exact| against the oracle's exact time stepping on the full grid"
+    return acc, ts
+
+
+def cpu_baseline_obj(w, nt_sample=256, solutions=None, all_cores=True):
     """The timed oracle legs; `solutions` (name -> host solution of the full workload) are
     compared with the oracle's exact solution, which the time-stepping leg produces."""
     nt_sample = min(nt_sample, w["NT"])
     s = oracle_sample(w, nt_sample)
-    ts = oracle_time_stepping(w)
-    acc = None
-    if solutions:
-        ue = ts["u"]
-        scale = float(np.abs(ue).max())
-        acc = {name: float(np.abs(v - ue).max() / scale) for name, v in solutions.items()}
-        acc["what"] = "max |u - u_exact| / max |u_exact| against the oracle's exact time stepping on the full grid"
-    return {"value": s["value"], "unit": "DOF/s", "cores": 1, "kind": "oracle",
-            "sample": "oracle STMG (FP64 C, Alg. 1 with the same options) solving the first %d of %d time steps "
-                      "of the workload (%d DOFs, same dx, dt, material and load) to %.0e: %d cycles in %.1f s"
-                      % (nt_sample, w["NT"], s["dofs"], TOL, s["cycles"], s["seconds"]),
-            "time_stepping": {"value": ts["value"], "unit": "DOF/s", "seconds": ts["seconds"],
-                              "what": "oracle exact sequential time stepping (Thomas per step) on the full grid"},
-            "accuracy": acc}
+    acc, ts = accuracy_against_exact(w, solutions or {})
+    out = {"value": s["value"], "unit": "DOF/s", "cores": 1, "kind": "oracle",
+           "sample": "oracle STMG (FP64 C, Alg. 1 with the same options) solving the first %d of %d time steps "
+                     "of the workload (%d DOFs, same dx, dt, material and load) to %.0e: %d cycles in %.1f s"
+                     % (nt_sample, w["NT"], s["dofs"], TOL, s["cycles"], s["seconds"]),
+           "host": cpu_model(),
+           "time_stepping": {"value": ts["value"], "unit": "DOF/s", "seconds": ts["seconds"],
+                             "what": "oracle exact sequential time stepping (Thomas per step) on the full grid"},
+           "accuracy": acc if solutions else None}
+    if all_cores:
+        try:
+            out["all_cores"] = oracle_all_cores(w["fn"], nt_sample)
+        except Exception as ex:  # report, do not hide
+            out["all_cores"] = {"error": repr(ex)}
+    return out
 
 
 def run_reference(args):
@@ -266,10 +331,10 @@ SERVING_MAX_NU = 240  # a request that does not converge is solved again with 2x
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture
 # of the kernel on the named workload; a kernel changed since its capture has no entry.
 NCU_TRAFFIC = {
-    ("filtered-simp-4096x16384", "k_sweep<double>"): 1.590e9,
-    ("filtered-simp-4096x16384", "k_defect (FP64, finest level)"): 1.3325e9,
-    ("filtered-simp-4096x16384", "k_stream UP + FP64 accumulate (finest level)"): 1.7477e9,
-    ("filtered-simp-4096x16384", "k_stream DOWN from zero (finest level)"): 0.6297e9,
+    ("4096x16384", "k_sweep<double>"): 1.590e9,
+    ("4096x16384", "k_defect (FP64, finest level)"): 1.3325e9,
+    ("4096x16384", "k_stream UP + FP64 accumulate (finest level)"): 1.7477e9,
+    ("4096x16384", "k_stream DOWN from zero (finest level)"): 0.6297e9,
 }
 
 
@@ -347,6 +412,38 @@ def run_serving(nreq, workers, inner=3, compare=8):
 
 
 # ----------------------------------------------------------------------------- GPU arm
+def timed_variant(pkg, w, k, c, q, u, precision, args, stream, world, rooflines=False):
+    """Solves of workload w (material k, c and element loads q on the device) in the given
+    precision, timed with CUDA events like the main leg; returns the record and the last
+    solution on the host."""
+    import torch
+
+    N, NT, L, tT = w["N"], w["NT"], w["L"], w["tT"]
+    dofs = (N + 1) * (NT + 1)
+    s2 = pkg.Solver(N, NT, L, tT, k, c, precision=precision, tol=TOL, **precision_opts(args, precision),
+                    **workload_opts(w, args))
+    for _ in range(max(1, args.warmup)):
+        s2.solve(u, q=q)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    st2 = [s2.solve(u, q=q) for _ in range(args.steps)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms2 = e0.elapsed_time(e1) / args.steps
+    rec = {"config": {"workload": w["name"], "N": N, "NT": NT, "dofs": dofs, "precision": precision,
+                      "k_ins": float(w["simp"][0]) if w.get("simp") is not None else None, "tol": TOL},
+           "precision": precision, "value": world * dofs / (ms2 * 1e-3), "unit": "DOF/s", "ms_per_step": ms2,
+           "cycles": st2[-1][1], "relres": st2[-1][2], "levels": s2.num_levels,
+           "converged": all(x[0] == "ok" and x[2] < TOL for x in st2),
+           "dtype": "f64" if precision == "fp64" else "f32+f64", **precision_opts(args, precision)}
+    if precision == "mixed" and rooflines:
+        rec["rooflines"] = mixed_rooflines(s2, stream, "%dx%d" % (N, NT), dofs, w.get("nu", 5))
+    s2.close()
+    return rec, u.cpu().numpy()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -440,7 +537,7 @@ def main():
         ach = flops / (sweep_ms * 1e-3) / 1e12
         roofline = {"kernel": "k_sweep<double> (finest level)", "bound": "alu", "achieved": ach,
                     "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s", "frac": ach / NOMINAL_FP64_TFLOPS,
-                    "traffic": NCU_TRAFFIC.get((w["name"], "k_sweep<double>")), "ms_per_launch": sweep_ms,
+                    "traffic": NCU_TRAFFIC.get(("%dx%d" % (N, NT), "k_sweep<double>")), "ms_per_launch": sweep_ms,
                     "hbm_gbs": bytes_alg / (sweep_ms * 1e-3) / 1e9,
                     "hbm_frac_of_measured": bytes_alg / (sweep_ms * 1e-3) / 1e9 /
                     measured_peaks().get("hbm_gbs", 6788.3),
@@ -488,34 +585,32 @@ def main():
                "d2h_bytes_per_step": int(uh.numel() * 8 + 8 * (cycles + 2)), "steps": ksteps}
         del qh, uh
 
-    # ---- the other precision on the same workload (same metric, same tolerance) ----
-    variant = None
+    # ---- the other precision on the same workload, and the k_ins = 1e-6 field of the same
+    # grid in the mixed scheme (same metric, same tolerance) ----
+    variant, variant_same_field = None, None
     if not args.no_variant:
         other = "mixed" if args.precision == "fp64" else "fp64"
-        s2 = pkg.Solver(N, NT, L, tT, k, c, precision=other, tol=TOL, **precision_opts(args, other), **workload_opts(w, args))
-        for _ in range(max(1, args.warmup)):
-            s2.solve(u, q=q)
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        st2 = [s2.solve(u, q=q) for _ in range(args.steps)]
-        e1.record(stream)
-        torch.cuda.synchronize()
+        variant_same_field, u2 = timed_variant(pkg, w, k, c, q, u, other, args, stream, world,
+                                               rooflines=args.workload != "filtered_simp")
         if check:
-            solutions[other] = u.cpu().numpy()
-        ms2 = e0.elapsed_time(e1) / args.steps
-        variant = {"precision": other, "value": world * dofs / (ms2 * 1e-3), "unit": "DOF/s", "ms_per_step": ms2,
-                   "cycles": st2[-1][1], "relres": st2[-1][2],
-                   "converged": all(x[0] == "ok" and x[2] < TOL for x in st2),
-                   "dtype": "f64" if other == "fp64" else "f32+f64", **precision_opts(args, other)}
-        if other == "mixed":
-            variant["rooflines"] = mixed_rooflines(s2, stream, w["name"], dofs, w.get("nu", 5))
-        s2.close()
+            solutions[other] = u2
+        if args.precision == "fp64" and args.workload == "filtered_simp":
+            w3 = load_workload("filtered_simp_high_contrast")
+            chi3 = torch.tensor(w3["chi"], device=dev)
+            k3, c3 = torch.empty_like(k), torch.empty_like(c)
+            pkg.simp(chi3, w3["simp"], k3, c3)
+            q3 = torch.tensor(w3["q"], device=dev)
+            variant, u3 = timed_variant(pkg, w3, k3, c3, q3, u, "mixed", args, stream, world, rooflines=True)
+            if check:
+                variant["accuracy"], _ = accuracy_against_exact(w3, {"mixed": u3})
+            del chi3, k3, c3, q3, u3
+        else:
+            variant, variant_same_field = variant_same_field, None
+        del u2
 
     # ---- serving: continuous batching of the uneven forward/adjoint request trace ----
     serving = None
-    if args.serving_requests > 0:
+    if args.serving_requests > 0 and world == 1:  # one GPU's server; replicas under torchrun skip it
         del u, q
         solver.close()
         torch.cuda.empty_cache()
@@ -523,7 +618,7 @@ def main():
 
     cpu = None
     if check:
-        cpu = cpu_baseline_obj(w, solutions=solutions)
+        cpu = cpu_baseline_obj(w, solutions=solutions, all_cores=not args.no_all_cores)
         del solutions
 
     if rank == 0:
@@ -538,7 +633,8 @@ def main():
                        "l2": "no flush: every vector (%d MB) exceeds the 129 MB L2" % (dofs * 8 // 2 ** 20),
                        "parallelism": "replicas" if world > 1 else "single"},
             "clocks": clocks, "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline,
-            "cpu_baseline": cpu, "variant": variant, "gpu_time_stepping": gpu_ts, "serving": serving,
+            "cpu_baseline": cpu, "variant": variant, "variant_same_field": variant_same_field,
+            "gpu_time_stepping": gpu_ts, "serving": serving,
             "accuracy": cpu.pop("accuracy", None) if cpu else None,
         }
         print(json.dumps(out))

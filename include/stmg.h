@@ -160,6 +160,10 @@ stmg_status stmg_assemble_load(stmg_t handle, const double* q_el, double* b);
  * ((nt+1) x (nel+1)) is non-NULL.  u: (nt+1) x (nel+1) output; with warm != 0 its
  * content is the initial guess (warm restart, Sec. 7.2), else the guess is 0.
  * cycles / relres (may be NULL) receive the cycle count and ||J u - b|| / ||b||.
+ * relres is the termination norm of the Sec. 3.1 rule as the solver evaluates it: ||b||^2
+ * is summed in FP64, and the residual's squares are formed from its FP64 value rounded to
+ * FP32 (after scaling by a power of two), summed in FP32 within each thread and in FP64
+ * across threads, so it agrees with the exact FP64 norm to about 1e-6 relative.
  * Returns STMG_OK, STMG_EDIVERGED or STMG_EMAXITER (u filled in all three cases). */
 stmg_status stmg_solve(stmg_t handle, const double* q_el, const double* b_nodal, double* u, int warm, int* cycles,
                        double* relres);
@@ -195,6 +199,17 @@ stmg_status stmg_sensitivity_slabs(stmg_t handle, const double* chi, const doubl
 
 /* Theta = b^T u dt / theta_ref (Sec. 7.1); theta: host output. */
 stmg_status stmg_objective(stmg_t handle, const double* b, const double* u, double theta_ref, double* theta);
+/* Gradient of the compliance of Sec. 7.1 with respect to the state, times a seed:
+ * grad_u = seed * dTheta/du = seed * b dt / theta_ref (with seed = 1 the right-hand side of
+ * the adjoint system of Sec. 7.2).  b, grad_u: (nt+1) x (nel+1) device arrays (grad_u may
+ * equal b); host arrays give STMG_EINVAL. */
+stmg_status stmg_objective_gradient(stmg_t handle, const double* b, double theta_ref, double seed, double* grad_u);
+/* Design-independent effective diffusivity of Sec. 7.2 for the SIMP model simp6 (host
+ * array as in stmg_simp): D_eff = sqrt(min D_SIMP * max D_SIMP), D_SIMP(chi) =
+ * k(chi) / c(chi), with the extrema taken over chi = j / 10000, j = 0..10000 (they need
+ * not lie at chi = 0 or 1).  Host-only arithmetic; deff: host output.  Use it as
+ * stmg_opts.deff_fixed for a hierarchy that every design of an optimisation shares. */
+stmg_status stmg_deff_simp(const double* simp6, double* deff);
 
 /* ---- optimisation loop (Sec. 7) ------------------------------------------------------ */
 /* One design update of the optimisation loop of Sec. 7.2.  The paper updates the design

@@ -11,7 +11,7 @@ import ctypes as C
 from . import _binding as B
 from ._binding import STMGError
 
-__all__ = ["Solver", "STMGError", "simp", "lib", "kernel_launches"]
+__all__ = ["Solver", "STMGError", "simp", "deff_simp", "lib", "kernel_launches"]
 
 lib = B.lib
 
@@ -28,6 +28,14 @@ def simp(chi, simp6, k, c, stream=None):
                            stream if stream is not None else B.default_stream())
     B.check(st)
     return k, c
+
+
+def deff_simp(simp6):
+    """Design-independent D_eff of Sec. 7.2 for the SIMP parameters (``stmg_deff_simp``)."""
+    s = (C.c_double * 6)(*[float(v) for v in simp6])
+    out = C.c_double(0.0)
+    B.check(B.lib().stmg_deff_simp(s, C.byref(out)))
+    return out.value
 
 
 def design_update(chi, g, vol_frac, move, out, stream=None):
@@ -137,9 +145,17 @@ class Solver:
         return g
 
     def objective(self, b, u, theta_ref=1.0):
+        """Theta = b^T u dt / theta_ref (Sec. 7.1), ``stmg_objective``."""
         out = C.c_double(0.0)
         B.check(B.lib().stmg_objective(self._h, B.ptr(b), B.ptr(u), float(theta_ref), C.byref(out)), self._h)
         return out.value
+
+    def objective_gradient(self, b, grad_u, theta_ref=1.0, seed=1.0):
+        """grad_u = seed * b dt / theta_ref, the gradient of Theta in u
+        (``stmg_objective_gradient``; device arrays)."""
+        B.check(B.lib().stmg_objective_gradient(self._h, B.ptr(b), float(theta_ref), float(seed), B.ptr(grad_u)),
+                self._h)
+        return grad_u
 
     # -- hierarchy -------------------------------------------------------------------
     @property

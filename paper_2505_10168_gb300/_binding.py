@@ -86,6 +86,8 @@ _SIGS = {
     "stmg_solve_adjoint": (_i, [_vp, _vp, _vp, _i, _ip, _dp]),
     "stmg_sensitivity": (_i, [_vp, _vp, _dp, _vp, _vp, _vp]),
     "stmg_objective": (_i, [_vp, _vp, _vp, _d, _dp]),
+    "stmg_objective_gradient": (_i, [_vp, _vp, _d, _d, _vp]),
+    "stmg_deff_simp": (_i, [_dp, _dp]),
     "stmg_recompute_slabs": (_i, [_vp, _vp, _vp, _i, _vp]),
     "stmg_sensitivity_slabs": (_i, [_vp, _vp, _dp, _vp, _vp, _i, _vp, _vp]),
     "stmg_num_levels": (_i, [_vp]),

@@ -73,6 +73,26 @@ def solve(chi, q, solver: Solver, simp6, slab_rows: int = 0):
     return _SolveFn.apply(chi, q, solver, simp6, int(slab_rows))
 
 
-def compliance(u, b, dt, theta_ref=1.0):
-    """Theta = b^T u dt / Theta_ref (Sec. 7.1), differentiable in u."""
-    return (b * u).sum() * (dt / theta_ref)
+class _ComplianceFn(torch.autograd.Function):
+    """Theta = b^T u dt / Theta_ref by stmg_objective; the backward hands b dt / Theta_ref
+    (times the upstream gradient) to u by stmg_objective_gradient."""
+
+    @staticmethod
+    def forward(ctx, u, b, solver, theta_ref):
+        ctx.save_for_backward(b)
+        ctx.solver, ctx.theta_ref = solver, float(theta_ref)
+        theta = solver.objective(b.contiguous(), u.contiguous(), ctx.theta_ref)
+        return torch.tensor(theta, dtype=torch.float64, device=u.device)
+
+    @staticmethod
+    def backward(ctx, grad_theta):
+        (b,) = ctx.saved_tensors
+        grad_u = torch.empty_like(b)
+        ctx.solver.objective_gradient(b.contiguous(), grad_u, ctx.theta_ref, float(grad_theta))
+        return grad_u, None, None, None
+
+
+def compliance(u, b, solver: Solver, theta_ref=1.0):
+    """Theta = b^T u dt / Theta_ref (Sec. 7.1) of the state u for the nodal load b on the
+    solver's grid, differentiable in u (forward and backward in the library)."""
+    return _ComplianceFn.apply(u, b, solver, float(theta_ref))

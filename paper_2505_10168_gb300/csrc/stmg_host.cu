@@ -23,6 +23,10 @@ namespace {
 
 thread_local std::string g_global_error;
 
+// Samples of chi in [0, 1] (both ends included: kDeffSamples + 1 points) over which the
+// design-independent D_eff of Sec. 7.2 takes the extrema of D_SIMP = k_SIMP / c_SIMP.
+constexpr int kDeffSamples = 10000;
+
 // One level of the hierarchy.
 struct Level {
   int N = 0, NT = 0, pitch = 0, next = STMG_COARSEST;
@@ -1349,6 +1353,37 @@ stmg_status stmg_objective(stmg_t h, const double* b, const double* u, double th
   double s = 0.0;
   CKS(read_scalar(h, h->scal, &s));
   *theta = s * L.dt / theta_ref;
+  return STMG_OK;
+}
+
+stmg_status stmg_objective_gradient(stmg_t h, const double* b, double theta_ref, double seed, double* grad_u) {
+  if (!h) return fail(nullptr, STMG_EINVAL, "NULL handle");
+  if (!b || !grad_u || !(theta_ref != 0.0) || !std::isfinite(seed))
+    return fail(h, STMG_EINVAL, "bad stmg_objective_gradient arguments");
+  if (!is_device_ptr(b) || !is_device_ptr(grad_u))
+    return fail(h, STMG_EINVAL, "stmg_objective_gradient takes device arrays");
+  const Level& L = h->lev[0];
+  const size_t n = (size_t)(L.NT + 1) * (size_t)(L.N + 1);
+  CK(launch_scaled_copy(n, seed * L.dt / theta_ref, b, grad_u, h->s));
+  CK(cudaStreamSynchronize(h->s));
+  return STMG_OK;
+}
+
+stmg_status stmg_deff_simp(const double* simp6, double* deff) {
+  if (!simp6 || !deff) return fail(nullptr, STMG_EINVAL, "bad stmg_deff_simp arguments");
+  for (int i = 0; i < 6; ++i)
+    if (!std::isfinite(simp6[i])) return fail(nullptr, STMG_EINVAL, "stmg_deff_simp: non-finite SIMP parameter");
+  const double kins = simp6[0], kcon = simp6[1], cins = simp6[2], ccon = simp6[3], pk = simp6[4], pc = simp6[5];
+  if (!(kins > 0.0 && kcon > 0.0 && cins > 0.0 && ccon > 0.0 && pk >= 0.0 && pc >= 0.0))
+    return fail(nullptr, STMG_EINVAL, "stmg_deff_simp: need positive k_ins, k_con, c_ins, c_con and p_k, p_c >= 0");
+  double dmin = INFINITY, dmax = 0.0;
+  for (int j = 0; j <= kDeffSamples; ++j) {
+    const double x = (double)j / kDeffSamples;
+    const double d = (kins + std::pow(x, pk) * (kcon - kins)) / (cins + std::pow(x, pc) * (ccon - cins));
+    dmin = std::min(dmin, d);
+    dmax = std::max(dmax, d);
+  }
+  *deff = std::sqrt(dmin * dmax);
   return STMG_OK;
 }
 

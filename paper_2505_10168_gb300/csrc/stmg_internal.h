@@ -227,6 +227,8 @@ cudaError_t launch_rhs32(const LevelView<double>& lv, const double* bs, const in
 cudaError_t launch_add_correction(size_t n, double* u, const float* e, const int* kexp, cudaStream_t s);
 // a . b over the padded arrays (padding is zero) into out[0]; deterministic.
 cudaError_t launch_dot(size_t n, const double* a, const double* b, double* partials, double* out, cudaStream_t s);
+// y[i] = alpha x[i] for i < n (y may equal x).
+cudaError_t launch_scaled_copy(size_t n, double alpha, const double* x, double* y, cudaStream_t s);
 
 // Coefficient arrays of a level from per-element k, c (device, FP64).
 cudaError_t launch_build_coef(int N, int pitch, double dx, double dt, double W, double omega, const double* k,

@@ -650,6 +650,12 @@ __global__ void __launch_bounds__(kThreads) k_dot(size_t n, const double* __rest
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
+__global__ void __launch_bounds__(kThreads) k_scaled_copy(size_t n, double alpha, const double* __restrict__ x,
+                                                          double* __restrict__ y) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    y[i] = alpha * x[i];
+}
+
 __global__ void __launch_bounds__(kThreads) k_add_correction(size_t n, double* __restrict__ u,
                                                              const float* __restrict__ e,
                                                              const int* __restrict__ kexp) {
@@ -975,6 +981,13 @@ cudaError_t launch_rhs32(const LevelView<double>& lv, const double* bs, const in
 
 cudaError_t launch_add_correction(size_t n, double* u, const float* e, const int* kexp, cudaStream_t s) {
   k_add_correction<<<blocks_for((long long)n), kThreads, 0, s>>>(n, u, e, kexp);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scaled_copy(size_t n, double alpha, const double* x, double* y, cudaStream_t s) {
+  const long long blocks = std::min<long long>(blocks_for((long long)n), 8LL * kNormBlocks);
+  k_scaled_copy<<<(unsigned)std::max<long long>(1, blocks), kThreads, 0, s>>>(n, alpha, x, y);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -124,12 +124,36 @@ struct Idle {
   long long bytes;
 };
 
+template <class T>
+void append_field(std::string& k, const T& v) {
+  k.append(reinterpret_cast<const char*>(&v), sizeof(v));
+}
+
+// Cache key of a request's hierarchy: the grid and every option field, one by one, so
+// that the struct's padding bytes (whatever a caller left in them) never enter the key.
 std::string job_key(const Job& j) {
-  std::string k(reinterpret_cast<const char*>(&j.opts), sizeof(j.opts));
-  k.append(reinterpret_cast<const char*>(&j.nel), sizeof(j.nel));
-  k.append(reinterpret_cast<const char*>(&j.nt), sizeof(j.nt));
-  k.append(reinterpret_cast<const char*>(&j.L), sizeof(j.L));
-  k.append(reinterpret_cast<const char*>(&j.tT), sizeof(j.tT));
+  const stmg_opts& o = j.opts;
+  std::string k;
+  append_field(k, o.nu);
+  append_field(k, o.omega);
+  append_field(k, o.lambda_crit);
+  append_field(k, o.interp);
+  append_field(k, o.reassembly);
+  append_field(k, o.min_nel);
+  append_field(k, o.num_levels);
+  append_field(k, o.max_levels);
+  append_field(k, o.max_coarse_dofs);
+  append_field(k, o.deff_fixed);
+  append_field(k, o.precision);
+  append_field(k, o.tol);
+  append_field(k, o.div_tol);
+  append_field(k, o.max_cycles);
+  append_field(k, o.mixed_first_cycles);
+  append_field(k, o.mixed_inner_cycles);
+  append_field(k, j.nel);
+  append_field(k, j.nt);
+  append_field(k, j.L);
+  append_field(k, j.tT);
   return k;
 }
 

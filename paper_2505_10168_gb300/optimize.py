@@ -14,21 +14,10 @@ in for the paper's MMA optimiser.  The loop stops when Theta has changed by less
 """
 from __future__ import annotations
 
-import math
-
 import numpy as np
 import torch
 
-from . import Solver, design_update, simp
-
-
-def deff_simp(simp6, samples=10001):
-    """Design-independent D_eff of Sec. 7.2: sqrt(min D_SIMP * max D_SIMP) over chi in [0, 1],
-    D_SIMP = k_SIMP / c_SIMP, taken over a fine grid of chi that includes both ends."""
-    k_ins, k_con, c_ins, c_con, pk, pc = (float(v) for v in simp6)
-    x = np.linspace(0.0, 1.0, samples)
-    d = (k_ins + x ** pk * (k_con - k_ins)) / (c_ins + x ** pc * (c_con - c_ins))
-    return math.sqrt(d.min() * d.max())
+from . import Solver, deff_simp, design_update, simp
 
 
 def optimize(N, NT, L, tT, simp6, q, vol_frac=0.5, move=0.2, chi0=0.5, theta_ref=1e6, warm=True, max_iter=200,

@@ -112,3 +112,24 @@ def test_noalloc_placement_rule(tmp_path):
                    capture_output=True)
     out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
     assert out == ["0"]
+
+
+def test_deff_simp_on_the_host():
+    """stmg_deff_simp (Sec. 7.2): sqrt(min D * max D) of D_SIMP = k_SIMP / c_SIMP over chi in
+    [0, 1], host arithmetic only.  With c constant the extrema are k_ins and k_con; with a
+    penalised c the minimum lies inside (0, 1), where a bounded scalar minimiser finds it."""
+    import math
+
+    import paper_2505_10168_gb300 as pkg
+
+    assert pkg.deff_simp([1e-3, 1.0, 1.0, 1.0, 3.0, 1.0]) == pytest.approx(math.sqrt(1e-3), rel=1e-15)
+    assert pkg.deff_simp([1e-6, 2.0, 0.5, 0.5, 3.0, 2.0]) == pytest.approx(math.sqrt(2e-6 / 0.25), rel=1e-15)
+    s6 = [0.01, 1.0, 0.1, 1.0, 3.0, 1.0]
+    d = lambda x: (0.01 + 0.99 * x ** 3) / (0.1 + 0.9 * x)  # noqa: E731
+    from scipy.optimize import minimize_scalar
+
+    m = minimize_scalar(d, bounds=(0.0, 1.0), method="bounded", options={"xatol": 1e-12})
+    assert 0.0 < m.x < 1.0 and m.fun < d(0.0)
+    assert pkg.deff_simp(s6) == pytest.approx(math.sqrt(m.fun * d(1.0)), rel=1e-7)
+    with pytest.raises(_binding.STMGError):
+        pkg.deff_simp([0.0, 1.0, 1.0, 1.0, 3.0, 1.0])

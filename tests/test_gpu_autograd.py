@@ -61,7 +61,7 @@ def test_autograd_compliance_gradient_matches_oracle(slab_rows):
     u = ag.solve(chi, q, solver, s6, slab_rows=slab_rows)
     b = torch.empty_like(u)
     solver.assemble_load(q, b)
-    theta = ag.compliance(u, b, solver.dt)
+    theta = ag.compliance(u, b, solver)
     theta.backward()
     ko, co = oracle.simp(w["chi"], s6)
     bo = oracle.assemble_load(N, NT, 1.0 / N, w["q"])
@@ -85,7 +85,7 @@ def test_random_design_gradient_against_central_differences():
     u = ag.solve(chi, q, solver, s6, slab_rows=256)
     b = torch.empty_like(u)
     solver.assemble_load(q, b)
-    ag.compliance(u, b, solver.dt).backward()
+    ag.compliance(u, b, solver).backward()
     grad = chi.grad.cpu().numpy()
     bo = oracle.assemble_load(N, NT, 1.0 / N, w["q"])
     dt = 1.0 / NT

@@ -179,16 +179,20 @@ def test_fp32_cycle_at_window_boundaries(N, adj):
 
 
 def test_mixed_single_level_and_tiny_grids():
-    """No coarsening (a one-level hierarchy) and grids narrower than one lane's columns."""
+    """No coarsening (a one-level hierarchy) and grids narrower than one lane's columns,
+    solved to 1e-10 so that the error bar of the mixed scheme (1e-8) is met whatever the
+    conditioning of these tiny random systems."""
     for N, NT in ((1, 1), (3, 5), (6, 10)):
         k, c = _rand_material(400 + N, N, 10.0)
-        g, o = _pair(N, NT, 1.0, 1.0, k, c, max_coarse_dofs=1, precision="mixed", tol=1e-8)
+        g, o = _pair(N, NT, 1.0, 1.0, k, c, max_coarse_dofs=1, precision="mixed", tol=1e-10)
         b = _rand_vec(8, o.shape(0))
         u = np.empty(o.shape(0))
         st, cyc, rr = g.solve(u, b=b)
-        assert st == "ok" and rr < 1e-8
+        assert st == "ok" and rr < 1e-10
         ue = oracle.exact(N, NT, 1.0, 1.0, k, c, b)
-        assert rel(u, ue) < 1e-6
+        err = rel(u, ue)
+        print("mixed %d x %d: cycles %d relres %.2e error %.2e" % (N, NT, cyc, rr, err))
+        assert err < 1e-8
         g.close()
 
 
@@ -291,6 +295,13 @@ def test_rod_blocks_solve_matches_oracle(reasm):
     ue = oracle.exact(N, NT, L, tT, w["k"], w["c"], b)
     assert rel(N_(ug), ue) < 1e-9
     g.close()
+    # the FP64 error bar against the exact solution (1e-10) at a residual well below it
+    g = pkg.Solver(N, NT, L, tT, T(w["k"]), T(w["c"]), reassembly=reasm, tol=1e-12)
+    st, cyc, rr = g.solve(ug, q=T(w["q"]))
+    err = rel(N_(ug), ue)
+    print("rod_blocks %s tol 1e-12: cycles %d relres %.2e error %.2e" % (reasm, cyc, rr, err))
+    assert st == "ok" and err < 1e-10
+    g.close()
 
 
 def test_host_and_device_arrays_agree():
@@ -374,7 +385,9 @@ def test_mixed_precision_reaches_fp64_residual(adj, inner):
     H = oracle.Hierarchy(N, NT, L, tT, ko, co, num_levels=1)
     r = H.residual(0, N_(u), bo, adj=adj)
     assert np.linalg.norm(r) / np.linalg.norm(bo) < 1e-8
-    assert rel(N_(u), ue) < 1e-5
+    err = rel(N_(u), ue)
+    print("mixed 512 x 2048 adj=%s inner=%d: cycles %d relres %.2e error %.2e" % (adj, inner, cyc, rr, err))
+    assert err < 1e-8
     g.close()
 
 
@@ -430,11 +443,14 @@ def test_warm_restart_converges_in_fewer_cycles():
     g.close()
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_full_size_filtered_simp_against_exact_solution(precision):
-    """The 4096 x 16384 workload in the launch configuration the benchmark times,
-    solved to 1e-8, checked against the oracle's exact time-stepping solution."""
-    w = wl.filtered_simp()
+@pytest.mark.parametrize("workload,precision", [("filtered_simp", "fp64"), ("filtered_simp", "mixed"),
+                                                ("filtered_simp_high_contrast", "mixed")])
+def test_full_size_filtered_simp_against_exact_solution(workload, precision):
+    """The 4096 x 16384 workloads (k_ins 1e-4, and 1e-6 for the mixed scheme) in the
+    launch configuration the benchmark times, solved to relative residual 1e-8 and checked
+    against the oracle's exact time-stepping solution to the stated bars: 1e-10 in FP64,
+    1e-8 in mixed precision."""
+    w = getattr(wl, workload)()
     N, NT, L, tT = w["N"], w["NT"], w["L"], w["tT"]
     ko, co = oracle.simp(w["chi"], w["simp"])
     g = pkg.Solver(N, NT, L, tT, T(ko), T(co), precision=precision, tol=1e-8)
@@ -446,7 +462,7 @@ def test_full_size_filtered_simp_against_exact_solution(precision):
     ue = oracle.exact(N, NT, L, tT, ko, co, bo)
     err = rel(N_(u), ue)
     print("%s %s: cycles %d relres %.3e max rel err vs exact %.3e" % (w["name"], precision, cyc, rr, err))
-    assert err < 1e-5, err
+    assert err < (1e-10 if precision == "fp64" else 1e-8), err
     g.close()
 
 
