@@ -296,10 +296,11 @@ def test_rod_blocks_solve_matches_oracle(reasm):
     assert rel(N_(ug), ue) < 1e-9
     g.close()
     # the FP64 error bar against the exact solution (1e-10) at a residual well below it
-    g = pkg.Solver(N, NT, L, tT, T(w["k"]), T(w["c"]), reassembly=reasm, tol=1e-12)
+    # (the FP64 residual floor of this problem is ~1.3e-12, measured)
+    g = pkg.Solver(N, NT, L, tT, T(w["k"]), T(w["c"]), reassembly=reasm, tol=1e-11)
     st, cyc, rr = g.solve(ug, q=T(w["q"]))
     err = rel(N_(ug), ue)
-    print("rod_blocks %s tol 1e-12: cycles %d relres %.2e error %.2e" % (reasm, cyc, rr, err))
+    print("rod_blocks %s tol 1e-11: cycles %d relres %.2e error %.2e" % (reasm, cyc, rr, err))
     assert st == "ok" and err < 1e-10
     g.close()
 
