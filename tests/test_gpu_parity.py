@@ -467,6 +467,33 @@ def test_full_size_filtered_simp_against_exact_solution(workload, precision):
     g.close()
 
 
+@pytest.mark.parametrize("i,interp,nu", [(0, "C", 5), (2, "C", 5), (2, "B", 5), (3, "C", 10)])
+@pytest.mark.parametrize("adj", [False, True])
+def test_mixed_solve_loop_matches_repeated_vcycles(i, interp, nu, adj):
+    """With one FP32 cycle per defect, the mixed solve loop (cold start: the first defect is
+    b' itself; then graph-captured FP32 V-cycles, each followed by the FP64 defect) runs the
+    same steps as repeated stmg_vcycle calls from zero (FP64 defect, one FP32 cycle, FP64
+    correction), so the iterates agree bit for bit (b is drawn with an RMS in [1, 2), where
+    the solve's FP32 scale is 2^0 like the V-cycle call's).  Cases: x- and causal
+    t-prolongation, bilinear t-prolongation, and nu = 10 (two passes per half-level)."""
+    N, NT, L, tT, k, c = _case(i)
+    g = pkg.Solver(N, NT, L, tT, T(k), T(c), precision="mixed", tol=1e-300, max_cycles=4, mixed_first_cycles=1,
+                   mixed_inner_cycles=1, max_coarse_dofs=64, interp=interp, nu=nu)
+    assert g.num_levels >= 3
+    b = 4.0 * (wl.uniform(90 + i, (NT + 1) * (N + 1)).reshape(NT + 1, N + 1) - 0.5)
+    b[0, :] = 0.0
+    b[:, 0] = 0.0
+    assert 1.0 <= np.sqrt(np.mean(b ** 2)) < 2.0
+    us = np.empty_like(b)
+    st, cyc, rr = g.solve_adjoint(us, b) if adj else g.solve(us, b=b)
+    assert st == "max_cycles" and cyc == 4, (st, cyc, rr)
+    uv = np.zeros_like(b)
+    for _ in range(cyc):
+        g.vcycle(uv, b, adjoint=adj)
+    assert np.array_equal(us, uv), rel(us, uv)
+    g.close()
+
+
 def test_mixed_pass_entry_point():
     """stmg_mixed_pass enqueues single steps of the mixed scheme on the solver's own vectors
     (for timing); it rejects other precisions, levels and kinds, and leaves the next cold
