@@ -528,13 +528,29 @@ stmg_status vcycle(stmg_t h, int l, bool adj, bool zero_init, bool first_done) {
   return STMG_OK;
 }
 
-// Split nu sweeps into passes of at most 5 fused sweeps.
-std::vector<int> sweep_passes(int nu) {
+// Split n sweeps into the fewest passes of at most `most` fused sweeps, of near-equal size.
+std::vector<int> split_sweeps(int n, int most) {
   std::vector<int> p;
-  const int k = (nu + 4) / 5;
-  for (int i = 0; i < k; ++i) p.push_back(nu / k + (i < nu % k ? 1 : 0));
+  const int k = (n + most - 1) / most;
+  for (int i = 0; i < k; ++i) p.push_back(n / k + (i < n % k ? 1 : 0));
   return p;
 }
+
+// Passes of a level's DOWN half: plain passes of at most 8 sweeps, then the pass that adds
+// the residual and the restriction, with at most 5 (a DOWN pass's window halo covers the
+// 5 sweeps, the residual and the restriction).  Every pass reads and writes the level's
+// vectors once, so fewer, deeper passes move fewer bytes (nu = 60: 8 passes instead of 12).
+std::vector<int> down_passes(int nu) {
+  if (nu <= 5) return {nu};
+  const int last = 5;
+  std::vector<int> p = split_sweeps(nu - last, 8);
+  p.push_back(last);
+  return p;
+}
+
+// Passes of a level's UP half: the prolongation and at most 8 sweeps, then plain passes of
+// at most 8.
+std::vector<int> up_passes(int nu) { return split_sweeps(nu, 8); }
 
 int* kexp(stmg_t h);
 
@@ -557,7 +573,7 @@ StreamArgs stream_args(const Level& L, double omega) {
 stmg_status down32(stmg_t h, int l, bool adj, bool zero_start, float** cur) {
   Level& L = h->lev[l];
   Level& C = h->lev[l + 1];
-  const std::vector<int> passes = sweep_passes(h->o.nu);
+  const std::vector<int> passes = down_passes(h->o.nu);
   const bool xc = L.next == STMG_XCOARSEN;
   float* in = zero_start ? nullptr : L.u32;
   float* out = zero_start ? L.u32 : L.t32;
@@ -590,7 +606,7 @@ stmg_status down32(stmg_t h, int l, bool adj, bool zero_start, float** cur) {
 stmg_status up32(stmg_t h, int l, bool adj, float* in, double* u64) {
   Level& L = h->lev[l];
   Level& C = h->lev[l + 1];
-  const std::vector<int> passes = sweep_passes(h->o.nu);
+  const std::vector<int> passes = up_passes(h->o.nu);
   const bool xc = L.next == STMG_XCOARSEN;
   float* out = (in == L.u32) ? L.t32 : L.u32;
   for (size_t p = 0; p < passes.size(); ++p) {

@@ -46,9 +46,19 @@ struct Width {
   static constexpr int kMinBlocks = kDown ? 1 : 4;    // 4-column passes: <= 128 registers
   static constexpr int kHalo = 8;                     // halo columns on each side
   static constexpr int kOwn = 32 * kVec - 2 * kHalo;  // columns owned per window
-  // S <= 5 sweeps and the residual spoil at most 6 columns from each window edge, and the
-  // x-restriction reads one more: the halo must cover 7 and be whole lanes.
-  static_assert(kHalo >= 7 && kHalo % kVec == 0, "halo must cover 7 columns in whole lanes");
+  // A DOWN pass's S <= 5 sweeps and the residual spoil at most 6 columns from each window
+  // edge, and the x-restriction reads one more; the S sweeps of a plain or UP pass spoil S
+  // columns (the prolongation is exact across the whole window).  The halo must cover 7
+  // and 8, and be whole lanes.
+  static constexpr int kMaxS = kDown ? 5 : 8;
+  static_assert(kHalo >= 7 && kHalo >= kMaxS && kHalo % kVec == 0, "halo must cover the spoiled columns in whole lanes");
+};
+
+// Resident blocks per SM the compiler plans registers for: more than 5 sweeps in a 4-column
+// pass hold more pipeline state than 128 registers.
+template <int MODE, int S>
+struct MinBlocks {
+  static constexpr int value = Width<MODE>::kDown ? Width<MODE>::kMinBlocks : (S <= 5 ? Width<MODE>::kMinBlocks : 3);
 };
 
 template <int V>
@@ -219,7 +229,8 @@ struct Pipe {
 // causal t-restriction, 3 x-prolongation + sweeps, 4 causal t-prolongation + sweeps,
 // 5 sweeps + residual + bilinear t-restriction, 6 bilinear t-prolongation + sweeps.
 template <bool ADJ, int S, int MODE>
-__global__ void __launch_bounds__(Width<MODE>::kThreads, Width<MODE>::kMinBlocks) k_stream(StreamArgs a) {
+__global__ void __launch_bounds__(Width<MODE>::kThreads, MinBlocks<MODE, S>::value) k_stream(StreamArgs a) {
+  static_assert(S >= 1 && S <= Width<MODE>::kMaxS, "sweeps per pass");
   using R = Ring<MODE>;
   using Wd = Width<MODE>;
   constexpr int kVec = Wd::kVec;
@@ -520,8 +531,17 @@ cudaError_t launch_mode(const StreamArgs& a, int S, cudaStream_t s) {
     case 3: return launch_k<ADJ, 3, MODE>(a, s);
     case 4: return launch_k<ADJ, 4, MODE>(a, s);
     case 5: return launch_k<ADJ, 5, MODE>(a, s);
-    default: return cudaErrorInvalidValue;
+    default: break;
   }
+  if constexpr (!Width<MODE>::kDown) {
+    switch (S) {
+      case 6: return launch_k<ADJ, 6, MODE>(a, s);
+      case 7: return launch_k<ADJ, 7, MODE>(a, s);
+      case 8: return launch_k<ADJ, 8, MODE>(a, s);
+      default: break;
+    }
+  }
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace

@@ -38,7 +38,8 @@ struct StreamArgs {
 // Fills rows / strips / chunks for a level of N elements and NT steps, windows owning `own`
 // columns, so that one wave of resident_warps warps covers it.
 void stream_layout(int N, int NT, int own, long long resident_warps, StreamArgs& a);
-// S sweeps (1..5) in one pass of the given mode; adj selects J^T.
+// S sweeps in one pass of the given mode (1..5 for the DOWN modes, 1..8 for the plain and
+// UP modes); adj selects J^T.
 cudaError_t launch_stream(int mode, bool adj, int S, const StreamArgs& a, cudaStream_t s);
 
 }  // namespace stmg

@@ -143,12 +143,14 @@ def test_vcycle_iterates_match_oracle(i, adj):
 
 @pytest.mark.parametrize("i", range(len(CASES)))
 @pytest.mark.parametrize("adj", [False, True])
-@pytest.mark.parametrize("nu", [5, 7])
+@pytest.mark.parametrize("nu", [5, 7, 16, 21])
 def test_fp32_cycle_matches_oracle_cycle(i, adj, nu):
     """One mixed-precision step from u = 0 is exactly one FP32 V-cycle on J e = b, so it
     must equal the oracle's FP64 V-cycle from zero up to FP32 rounding (amplified by the
     coarse solves); this checks the fused FP32 passes directly, which the outer FP64
-    correction would otherwise hide."""
+    correction would otherwise hide.  nu > 5 splits each half-level into passes: 7 gives a
+    DOWN half of 2 + 5 sweeps and one UP pass of 7; 16 gives 6 + 5 and 8 + 8; 21 gives
+    8 + 8 + 5 and 7 + 7 + 7."""
     N, NT, L, tT, k, c = _case(i)
     g, o = _pair(N, NT, L, tT, k, c, max_coarse_dofs=64, nu=nu, precision="mixed")
     b = _rand_vec(3, o.shape(0))
@@ -161,15 +163,17 @@ def test_fp32_cycle_matches_oracle_cycle(i, adj, nu):
 
 @pytest.mark.parametrize("N", [236, 240, 244, 480, 484, 728])
 @pytest.mark.parametrize("adj", [False, True])
-def test_fp32_cycle_at_window_boundaries(N, adj):
+@pytest.mark.parametrize("nu", [5, 16])
+def test_fp32_cycle_at_window_boundaries(N, adj, nu):
     """The fused passes split a level into windows of 240 (DOWN, 8 columns per lane) and
     112 (UP, 4 per lane) owned columns: widths on both sides of one, two and three windows,
-    with several x-coarsenings below, against the oracle's FP64 cycle from zero."""
+    with several x-coarsenings below, against the oracle's FP64 cycle from zero; nu = 16
+    runs passes of 8 sweeps, whose spoiled edge columns fill the whole 8-column halo."""
     NT = 48
     k, c = _rand_material(300 + N, N, 1e3)
     deff = np.sqrt((k / c).min() * (k / c).max())
     tT = 3.0 * (1.0 / N) ** 2 / deff * NT
-    g, o = _pair(N, NT, 1.0, tT, k, c, max_coarse_dofs=64, precision="mixed")
+    g, o = _pair(N, NT, 1.0, tT, k, c, max_coarse_dofs=64, precision="mixed", nu=nu)
     assert o.path().count("x") >= 2
     b = _rand_vec(7, o.shape(0))
     ug = np.zeros(o.shape(0))
