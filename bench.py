@@ -44,6 +44,8 @@ def parse():
     p.add_argument("--workload", default="filtered_simp", choices=sorted(WORKLOADS),
                    help="rod_blocks (128 x 128 two-phase blocks), filtered_simp (4096 x 16384, k_ins 1e-4), "
                         "filtered_simp_high_contrast (same grid, k_ins 1e-6), random_design (1024 x 4096, nu 20)")
+    p.add_argument("--grid", default="", help="NxNT: the workload's recipe on another grid (not rod_blocks), "
+                                                "e.g. a case small enough for a multi-pass ncu capture")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-variant", action="store_true", help="skip the other-precision solve of the same workload")
@@ -60,10 +62,14 @@ def parse():
 WORKLOADS = ("rod_blocks", "filtered_simp", "filtered_simp_high_contrast", "random_design")
 
 
-def load_workload(name):
+def load_workload(name, grid=""):
     from paper_2505_10168_gb300 import workloads as wl
 
-    w = getattr(wl, name)()
+    if grid:
+        n, nt = (int(v) for v in grid.lower().split("x"))
+        w = getattr(wl, name)(N=n, NT=nt)
+    else:
+        w = getattr(wl, name)()
     w["fn"] = name
     return w
 
@@ -264,7 +270,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    w = load_workload(args.workload)
+    w = load_workload(args.workload, args.grid)
     nt_sample = min(128, w["NT"])
     for _ in range(args.warmup):
         oracle_sample(w, nt_sample)
@@ -353,6 +359,8 @@ def mixed_rooflines(solver, stream, wname, dofs, nu, reps=20):
     for kind, name, nbytes, flops in (("defect", "k_defect (FP64, finest level)", 20.0, 12.0),
                                       ("up", "k_stream UP + FP64 accumulate (finest level)", 26.0, None),
                                       ("down", "k_stream DOWN from zero (finest level)", 10.0, None)):
+        # an NVTX range per step, so that a profiler can select these launches alone
+        torch.cuda.nvtx.range_push("roofline_" + kind)
         solver.mixed_pass(0, kind)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -361,6 +369,7 @@ def mixed_rooflines(solver, stream, wname, dofs, nu, reps=20):
             solver.mixed_pass(0, kind)
         e1.record(stream)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
         ms = e0.elapsed_time(e1) / reps
         gbs = nbytes * dofs / (ms * 1e-3) / 1e9
         if flops is None:
@@ -465,7 +474,7 @@ def main():
         if world > 1:
             dist.barrier()
 
-    w = load_workload(args.workload)
+    w = load_workload(args.workload, args.grid)
     N, NT, L, tT = w["N"], w["NT"], w["L"], w["tT"]
     dofs = (N + 1) * (NT + 1)
     stream = torch.cuda.current_stream(dev)
@@ -595,7 +604,7 @@ def main():
         if check:
             solutions[other] = u2
         if args.precision == "fp64" and args.workload == "filtered_simp":
-            w3 = load_workload("filtered_simp_high_contrast")
+            w3 = load_workload("filtered_simp_high_contrast", args.grid)
             chi3 = torch.tensor(w3["chi"], device=dev)
             k3, c3 = torch.empty_like(k), torch.empty_like(c)
             pkg.simp(chi3, w3["simp"], k3, c3)
