@@ -11,6 +11,13 @@ separately.  Every vector (537 MB in FP64) is larger than L2, so no flush is nee
 
 Under torchrun every rank solves its own copy (replicas, weak scaling) and rank 0
 prints one JSON line.  The roofline object is measured live on the dominant kernel.
+
+Besides the headline solve the line carries (one GPU): `variant` -- the same grid with
+k_ins = 1e-6 in the mixed scheme, with its error against the oracle's exact solution;
+`variant_same_field` -- the headline field in the mixed scheme; `other_configs` -- the
+128 x 128 two-phase rod (to 1e-10 in FP64, and to 1e-8 in both precisions) and one
+gradient step of the 1024 x 4096 differentiation workload through torch.autograd;
+`serving` -- the 512-request trace; `cpu_baseline` -- the oracle on the host cores.
 """
 from __future__ import annotations
 
@@ -55,6 +62,8 @@ def parse():
     p.add_argument("--serving-requests", type=int, default=512,
                    help="requests of the 512-request serving trace to replay (0: skip serving)")
     p.add_argument("--no-all-cores", action="store_true", help="skip the all-cores oracle timing")
+    p.add_argument("--no-other-configs", action="store_true",
+                   help="skip the 128 x 128 rod and the differentiation workload legs")
     p.add_argument("--serving-workers", type=int, default=6)
     return p.parse_args()
 
@@ -420,6 +429,89 @@ def run_serving(nreq, workers, inner=3, compare=8):
             "vs_fp64_single": vs}
 
 
+# ----------------------------------------------------------------------------- other configs
+def cuda_time(stream, fn, reps):
+    """Average ms of fn() over reps calls, CUDA events on the stream (after one warm-up)."""
+    import torch
+
+    fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    out = [fn() for _ in range(reps)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps, out[-1]
+
+
+def rod_blocks_leg(pkg, dev, stream, reps=10):
+    """The 128 x 128 two-phase rod (k in {1e-3, 1}, uniform load), solved to relative residual
+    1e-10 in FP64 as the workload states, and to 1e-8 (the metric) in both precisions;
+    errors against the oracle's exact time stepping."""
+    import torch
+
+    import oracle
+
+    w = load_workload("rod_blocks")
+    N, NT, L, tT = w["N"], w["NT"], w["L"], w["tT"]
+    dofs = (N + 1) * (NT + 1)
+    q = torch.tensor(w["q"], device=dev)
+    u = torch.empty((NT + 1, N + 1), dtype=torch.float64, device=dev)
+    ue = oracle.exact(N, NT, L, tT, w["k"], w["c"], oracle.assemble_load(N, NT, L / N, w["q"]))
+    out = {"workload": w["name"], "dofs": dofs, "solves": {}}
+    for name, prec, tol in (("fp64_1e-10", "fp64", 1e-10), ("fp64", "fp64", TOL), ("mixed", "mixed", TOL)):
+        s = pkg.Solver(N, NT, L, tT, w["k"], w["c"], precision=prec, tol=tol)
+        ms, st = cuda_time(stream, lambda: s.solve(u, q=q), reps)
+        err = float(np.abs(u.cpu().numpy() - ue).max() / np.abs(ue).max())
+        out["solves"][name] = {"precision": prec, "tol": tol, "value": dofs / (ms * 1e-3), "unit": "DOF/s",
+                               "ms_per_solve": ms, "cycles": st[1], "relres": st[2], "converged": st[0] == "ok",
+                               "error_vs_exact": err}
+        s.close()
+    return out
+
+
+def differentiation_leg(pkg, dev, stream, reps=3):
+    """The differentiation workload (1024 x 4096, densities U(0.05, 1), SIMP p = 3,
+    k_min = 1e-3, nu = 20): one gradient step through torch.autograd -- SIMP material, forward
+    STMG solve, compliance Theta = sum_n b_n^T u_n dt, adjoint STMG solve and the fused
+    sensitivity -- to relative residual 1e-8 in each precision, against the oracle's gradient
+    from exact time stepping (the central-difference check is in the tests)."""
+    import torch
+
+    import oracle
+    from paper_2505_10168_gb300 import autograd as ag
+
+    w = load_workload("random_design")
+    N, NT, L, tT, s6 = w["N"], w["NT"], w["L"], w["tT"], w["simp"]
+    dofs = (N + 1) * (NT + 1)
+    q = torch.tensor(w["q"], device=dev)
+    ko, co = oracle.simp(w["chi"], s6)
+    bo = oracle.assemble_load(N, NT, L / N, w["q"])
+    uo = oracle.exact(N, NT, L, tT, ko, co, bo)
+    lo = oracle.exact(N, NT, L, tT, ko, co, bo * (tT / NT), adj=True)
+    go = oracle.sensitivity(N, NT, L, tT, w["chi"], s6, uo, lo)
+    out = {"workload": w["name"], "dofs": dofs, "nu": w["nu"], "tol": TOL, "steps": {}}
+    for prec in ("fp64", "mixed"):
+        solver = pkg.Solver(N, NT, L, tT, ko, co, precision=prec, tol=TOL, nu=w["nu"], max_cycles=300)
+        b = torch.empty((NT + 1, N + 1), dtype=torch.float64, device=dev)
+        solver.assemble_load(q, b)
+
+        def step():
+            chi = torch.tensor(w["chi"], device=dev).requires_grad_(True)
+            u = ag.solve(chi, q, solver, s6)
+            theta = ag.compliance(u, b, solver)
+            theta.backward()
+            return chi.grad
+
+        ms, g = cuda_time(stream, step, reps)
+        gerr = float(np.abs(g.cpu().numpy() - go).max() / np.abs(go).max())
+        out["steps"][prec] = {"value": 2 * dofs / (ms * 1e-3), "unit": "DOF/s (forward + adjoint)",
+                              "ms_per_gradient": ms, "gradient_error_vs_oracle": gerr}
+        solver.close()
+    return out
+
+
 # ----------------------------------------------------------------------------- GPU arm
 def timed_variant(pkg, w, k, c, q, u, precision, args, stream, world, rooflines=False):
     """Solves of workload w (material k, c and element loads q on the device) in the given
@@ -617,6 +709,16 @@ def main():
             variant, variant_same_field = variant_same_field, None
         del u2
 
+    # ---- the other workloads: the 128 x 128 rod and the differentiation step ----
+    other_configs = None
+    if not args.no_other_configs and world == 1 and not args.grid:
+        other_configs = {}
+        for name, fn in (("rod_blocks", rod_blocks_leg), ("differentiation", differentiation_leg)):
+            try:
+                other_configs[name] = fn(pkg, dev, stream)
+            except Exception as ex:  # report, do not hide
+                other_configs[name] = {"error": repr(ex)}
+
     # ---- serving: continuous batching of the uneven forward/adjoint request trace ----
     serving = None
     if args.serving_requests > 0 and world == 1:  # one GPU's server; replicas under torchrun skip it
@@ -643,6 +745,7 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single"},
             "clocks": clocks, "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline,
             "cpu_baseline": cpu, "variant": variant, "variant_same_field": variant_same_field,
+            "other_configs": other_configs,
             "gpu_time_stepping": gpu_ts, "serving": serving,
             "accuracy": cpu.pop("accuracy", None) if cpu else None,
         }
