@@ -103,3 +103,27 @@ def test_random_design_gradient_against_central_differences():
         fd = (theta(xp) - theta(xm)) / (2 * h)
         assert abs(grad[e] - fd) <= 1e-5 * scale, (e, grad[e], fd)
     solver.close()
+
+
+def test_objective_and_its_gradient_in_the_library():
+    """stmg_objective gives Theta = b^T u dt / Theta_ref (Sec. 7.1) and
+    stmg_objective_gradient seed * b dt / Theta_ref, the adjoint right-hand side of Sec.
+    7.2; autograd.compliance uses both.  Host arrays are refused by the gradient call."""
+    N, NT = 64, 128
+    w, chi0, q = _cfg4(N, NT)
+    solver = pkg.Solver(N, NT, 1.0, 1.0, np.ones(N), np.ones(N))
+    b = torch.empty((NT + 1, N + 1), dtype=torch.float64, device=DEV)
+    solver.assemble_load(q, b)
+    u = T(wl.uniform(9, (NT + 1) * (N + 1)).reshape(NT + 1, N + 1))
+    theta = solver.objective(b, u, theta_ref=2.0)
+    bo = oracle.assemble_load(N, NT, 1.0 / N, w["q"])
+    assert theta == pytest.approx(oracle.objective(N, NT, solver.dt, bo, u.cpu().numpy()) / 2.0, rel=1e-13)
+    g = torch.empty_like(b)
+    solver.objective_gradient(b, g, theta_ref=2.0, seed=3.0)
+    assert torch.equal(g, b * (3.0 * solver.dt / 2.0))
+    uu = u.clone().requires_grad_(True)
+    ag.compliance(uu, b, solver, theta_ref=2.0).backward()
+    assert torch.equal(uu.grad, b * (solver.dt / 2.0))
+    with pytest.raises(pkg.STMGError, match="einval"):
+        solver.objective_gradient(b.cpu(), g)
+    solver.close()
