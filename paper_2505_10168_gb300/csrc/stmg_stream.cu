@@ -20,6 +20,10 @@
 // predicated store.  Each lane holds kVec consecutive columns, so the per-row bookkeeping
 // (ring, predicates, addresses, shuffles) is spread over that many DOFs.
 //
+// A pass runs S sweeps: up to 5 in a DOWN pass (plus the residual and the restriction) and
+// up to 8 in a plain or UP pass, as far as the 8-column halo keeps the owned columns exact;
+// more smoothing steps take several passes, each reading and writing the level once.
+//
 // HBM traffic per DOF of a level (x-coarsening, zero start): DOWN reads b' and writes u
 // and b'_c (10 B); UP reads u, b', z and writes u (14 B); the finest-level UP of the
 // mixed scheme adds its result straight into the FP64 iterate instead (26 B).
