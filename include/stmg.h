@@ -147,7 +147,8 @@ const char* stmg_last_error(stmg_t handle);
 
 /* SIMP material model (Sec. 2.1): k = k_ins + (k_con - k_ins) chi^p_k and
  * c = c_ins + (c_con - c_ins) chi^p_c with simp6 = {k_ins, k_con, c_ins, c_con, p_k, p_c}
- * (host array).  chi, k_el, c_el: nel values, all device memory.  stream may be NULL. */
+ * (host array).  chi, k_el, c_el: nel values, all device memory of the current device (or
+ * managed memory; anything else gives STMG_EINVAL).  stream may be NULL. */
 stmg_status stmg_simp(int nel, const double* chi, const double* simp6, double* k_el, double* c_el, void* stream);
 
 /* Nodal load b = B b_Neu from element loads q_el[(nt+1) x nel] (Sec. 2.2, Appendix A):

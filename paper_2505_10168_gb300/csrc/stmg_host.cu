@@ -14,6 +14,7 @@
 
 #include "stmg.h"
 #include "stmg_internal.h"
+#include "stmg_placement.h"
 #include "stmg_slab.h"
 #include "stmg_stream.h"
 
@@ -674,13 +675,21 @@ stmg_status copy_out(stmg_t h, double* dst, const double* src, int pitch, int ro
   return STMG_OK;
 }
 
+// Memory the current device's kernels can read directly: its own device memory or managed
+// memory.  Host memory and device memory of another GPU are not (calls stage them through
+// their own buffers, or refuse them where a call takes device arrays only).
 bool is_device_ptr(const void* p) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return noalloc_placement(static_cast<int>(a.type), a.device, dev) == kPlaceUsable;
 }
 
 // Element loads -> nodal b on level 0.
@@ -1272,6 +1281,8 @@ stmg_status stmg_update_material(stmg_t h, const double* k_el, const double* c_e
 stmg_status stmg_simp(int nel, const double* chi, const double* simp6, double* k_el, double* c_el, void* stream) {
   stmg_t h = nullptr;
   if (nel < 1 || !chi || !simp6 || !k_el || !c_el) return fail(nullptr, STMG_EINVAL, "bad stmg_simp arguments");
+  if (!is_device_ptr(chi) || !is_device_ptr(k_el) || !is_device_ptr(c_el))
+    return fail(nullptr, STMG_EINVAL, "stmg_simp takes arrays on the current device");
   Simp6 sp;
   for (int i = 0; i < 6; ++i) sp.v[i] = simp6[i];
   CK(launch_simp(nel, chi, sp, k_el, c_el, (cudaStream_t)stream));

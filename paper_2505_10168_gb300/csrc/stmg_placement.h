@@ -1,5 +1,6 @@
-// stmg_placement.h -- the pointer-placement rule of stmg_sensitivity_noalloc, kept free of
-// CUDA calls so that host-only tests can compile and check it.
+// stmg_placement.h -- the pointer-placement rule of the library's device-array checks
+// (stmg_sensitivity_noalloc, and every call that reads a caller's array in place), kept free
+// of CUDA calls so that host-only tests can compile and check it.
 //
 // type is the cudaMemoryType that cudaPointerGetAttributes reports for a pointer
 // (0 unregistered host, 1 registered host, 2 device, 3 managed), device its device

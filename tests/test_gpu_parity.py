@@ -332,6 +332,8 @@ def test_adjoint_solve_identity_and_sensitivity_random_design_small():
     pkg.simp(chi, w["simp"], k, c)
     ko, co = oracle.simp(w["chi"], w["simp"])
     assert rel(N_(k), ko) < 1e-15 and rel(N_(c), co) < 1e-15
+    with pytest.raises(pkg.STMGError, match="einval"):  # host arrays: refused, not read by a kernel
+        pkg.simp(np.ascontiguousarray(w["chi"]), w["simp"], np.empty(N), np.empty(N))
     # nu = 20 as in Sec. 6-7: with nu = 5 even the two-grid cycle diverges on this rough field
     g = pkg.Solver(N, NT, L, tT, k, c, tol=1e-11, nu=20)
     b = torch.empty((NT + 1, N + 1), dtype=torch.float64, device=DEV)
