@@ -133,3 +133,22 @@ def test_deff_simp_on_the_host():
     assert pkg.deff_simp(s6) == pytest.approx(math.sqrt(m.fun * d(1.0)), rel=1e-7)
     with pytest.raises(_binding.STMGError):
         pkg.deff_simp([0.0, 1.0, 1.0, 1.0, 3.0, 1.0])
+
+
+def test_grid_size_limit_on_the_host():
+    """A space-time vector is indexed with 32-bit DOF numbers: (nel+1)(nt+1) must stay
+    below 2^31.  The largest grid below the limit is planned (its footprint is positive);
+    the first one at the limit is refused by stmg_footprint and by stmg_create before any
+    device work, with a message."""
+    lib = _binding.lib()
+    o = _binding.make_opts()
+    import numpy as np
+
+    k = np.ones(32767)
+    assert (32767 + 1) * (65534 + 1) < 2 ** 31 and (32767 + 1) * (65535 + 1) == 2 ** 31
+    assert lib.stmg_footprint(32767, 65534, 1.0, 1.0, k.ctypes.data, k.ctypes.data, ctypes.byref(o)) > 0
+    assert lib.stmg_footprint(32767, 65535, 1.0, 1.0, k.ctypes.data, k.ctypes.data, ctypes.byref(o)) == -1
+    h = ctypes.c_void_p()
+    st = lib.stmg_create(ctypes.byref(h), 32767, 65535, 1.0, 1.0, k.ctypes.data, k.ctypes.data, None, None)
+    assert _binding.STATUS[st] == "einval" and not h.value
+    assert b"2^31" in lib.stmg_last_error(None)
