@@ -108,3 +108,33 @@ def test_smoothing_escalation_is_per_request():
                                     adjoint=r["adjoint"], out=one, **dict(opts, nu=x["nu"])))
         assert (y["status"], y["nu"], y["cycles"]) == (x["status"], x["nu"], x["cycles"])
         assert np.array_equal(o, one, equal_nan=True)
+
+
+def test_trace_requests_at_full_size():
+    """Requests of the 512-request serving trace as the benchmark serves them (mixed, nu =
+    60, tol 1e-8, up to 300 cycles, smoothing escalation): the largest one (3968 x 13888, 55 M
+    DOFs) and two adjoint ones, served together.  Each result's true FP64 residual, which the
+    oracle evaluates, is below the tolerance, and its error against the oracle's exact time
+    stepping is reported."""
+    trace = wl.serving_requests()
+    picks = [trace[430], trace[0], trace[2]]
+    assert picks[0]["N"] == 3968 and picks[0]["NT"] == 13888 and picks[1]["adjoint"] and picks[2]["adjoint"]
+    opts = dict(precision="mixed", tol=1e-8, nu=60, max_cycles=300)
+    outs = [np.full((r["NT"] + 1, r["N"] + 1), np.nan) for r in picks]
+    with sv.Server(workers=3, max_nu=240) as s:
+        ts = [s.submit(r["N"], r["NT"], r["L"], r["tT"], *wl.request_fields(r)[:2], q_value=1.0,
+                       adjoint=r["adjoint"], out=o, **opts) for r, o in zip(picks, outs)]
+        res = [s.result(t) for t in ts]
+    for r, o, x in zip(picks, outs, res):
+        k, c, q = wl.request_fields(r)
+        N, NT, L, tT = r["N"], r["NT"], r["L"], r["tT"]
+        b = oracle.assemble_load(N, NT, L / N, q)
+        if r["adjoint"]:
+            b = b * (tT / NT)
+        H = oracle.Hierarchy(N, NT, L, tT, k, c, num_levels=1)
+        rel = np.linalg.norm(H.residual(0, o, b, adj=r["adjoint"])) / np.linalg.norm(b)
+        ue = oracle.exact(N, NT, L, tT, k, c, b, adj=r["adjoint"])
+        err = np.abs(o - ue).max() / np.abs(ue).max()
+        print("%d x %d adj=%s: %s, %d cycles at nu %d, residual %.2e, error %.2e"
+              % (N, NT, r["adjoint"], x["status"], x["cycles"], x["nu"], rel, err))
+        assert x["status"] == "ok" and rel < 1e-8, (r["N"], r["NT"], x, rel)
