@@ -56,8 +56,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-variant", action="store_true", help="skip the other-precision solve of the same workload")
-    p.add_argument("--mixed-inner", type=int, default=3, help="FP32 V-cycles per FP64 defect in the mixed scheme")
-    p.add_argument("--mixed-first", type=int, default=3, help="FP32 V-cycles on the first defect in the mixed scheme")
+    p.add_argument("--mixed-inner", type=int, default=4, help="FP32 V-cycles per FP64 defect in the mixed scheme")
+    p.add_argument("--mixed-first", type=int, default=4, help="FP32 V-cycles on the first defect in the mixed scheme")
     p.add_argument("--max-coarse-dofs", type=int, default=0, help="planner: stop at a level this small (0: default)")
     p.add_argument("--serving-requests", type=int, default=512,
                    help="requests of the 512-request serving trace to replay (0: skip serving)")
@@ -339,7 +339,8 @@ def workload_opts(w, args=None):
     return o
 
 
-SERVING_OPTS = dict(precision="mixed", tol=TOL, nu=60, max_cycles=300)
+# the serving trace's solver options; 3 FP32 cycles per FP64 defect measured best at nu = 60
+SERVING_OPTS = dict(precision="mixed", tol=TOL, nu=60, max_cycles=300, mixed_first_cycles=3, mixed_inner_cycles=3)
 SERVING_MAX_NU = 240  # a request that does not converge is solved again with 2x the sweeps, up to this
 
 
@@ -393,7 +394,7 @@ def mixed_rooflines(solver, stream, wname, dofs, nu, reps=20):
     return out
 
 
-def run_serving(nreq, workers, inner=3, compare=8):
+def run_serving(nreq, workers, compare=8):
     """Closed loop (all requests queued at once) for throughput, then the same requests
     with their Poisson gaps rescaled to 0.5x, 0.8x and 1.0x that throughput for latency
     (0.8x is the headline p50/p99)."""
@@ -402,7 +403,7 @@ def run_serving(nreq, workers, inner=3, compare=8):
 
     reqs = wl.serving_requests()[:nreq]
     fields = lambda r: wl.request_fields(r)[:2]  # noqa: E731
-    opts = dict(SERVING_OPTS, mixed_inner_cycles=inner)
+    opts = dict(SERVING_OPTS)
     with sv.Server(workers=workers, max_nu=SERVING_MAX_NU) as srv:
         sv.replay(srv, reqs[: min(4, nreq)], fields, speed=1e9, **opts)  # warm-up
         _, closed = sv.replay(srv, reqs, fields, speed=1e9, **opts)
@@ -418,6 +419,7 @@ def run_serving(nreq, workers, inner=3, compare=8):
         _, batched = sv.replay(srv, sub, fields, speed=1e9, **opts)
     fp64_opts = dict(opts, precision="fp64")
     fp64_opts.pop("mixed_inner_cycles")
+    fp64_opts.pop("mixed_first_cycles")
     with sv.Server(workers=1, max_nu=SERVING_MAX_NU) as one:
         _, single = sv.replay(one, sub, fields, speed=1e9, **fp64_opts)
     vs = {"requests": len(sub), "mixed_batched": batched, "fp64_single": single,
@@ -730,7 +732,7 @@ def main():
         del u, q
         solver.close()
         torch.cuda.empty_cache()
-        serving = run_serving(args.serving_requests, args.serving_workers, args.mixed_inner)
+        serving = run_serving(args.serving_requests, args.serving_workers)
 
     cpu = None
     if check:

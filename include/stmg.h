@@ -85,9 +85,9 @@ typedef struct {
     double tol;                /* [1e-10] stop when ||J u - b|| / ||b|| < tol (Sec. 3.1) */
     double div_tol;            /* [1e9] stop (diverged) when the relative residual exceeds this */
     int max_cycles;            /* [100] cycle limit (Sec. 3.1) */
-    int mixed_first_cycles;    /* [3] STMG_MIXED: FP32 V-cycles run on the first defect (an inner
+    int mixed_first_cycles;    /* [4] STMG_MIXED: FP32 V-cycles run on the first defect (an inner
                                   iteration) before the first FP64 correction; each counts as a cycle */
-    int mixed_inner_cycles;    /* [3] STMG_MIXED: FP32 V-cycles run on every later defect (1..8), the
+    int mixed_inner_cycles;    /* [4] STMG_MIXED: FP32 V-cycles run on every later defect (1..8), the
                                   first from zero and the others continuing the FP32 iterate; the
                                   termination test is then taken every mixed_inner_cycles cycles */
 } stmg_opts;

@@ -1113,8 +1113,8 @@ void stmg_default_opts(stmg_opts* o) {
   o->tol = 1e-10;
   o->div_tol = 1e9;
   o->max_cycles = 100;
-  o->mixed_first_cycles = 3;
-  o->mixed_inner_cycles = 3;
+  o->mixed_first_cycles = 4;
+  o->mixed_inner_cycles = 4;
 }
 
 const char* stmg_last_error(stmg_t h) { return h ? h->err.c_str() : g_global_error.c_str(); }

@@ -386,7 +386,7 @@ def test_mixed_precision_reaches_fp64_residual(adj, inner):
     else:
         st, cyc, rr = g.solve(u, b=T(bo))
     assert st == "ok" and rr < 1e-8, (st, cyc, rr)
-    assert (cyc - 3) % inner == 0  # 3 first cycles, then whole groups of inner cycles
+    assert (cyc - 4) % inner == 0  # 4 first cycles (the default), then whole groups of inner cycles
     ue = oracle.exact(N, NT, L, tT, ko, co, bo, adj=adj)
     # true FP64 residual of the returned iterate, evaluated by the oracle
     H = oracle.Hierarchy(N, NT, L, tT, ko, co, num_levels=1)
