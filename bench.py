@@ -649,6 +649,7 @@ def main():
         e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
         solver.smooth(0, uu, b, 0)
         nsw = 20
+        torch.cuda.nvtx.range_push("roofline_sweep")  # lets a profiler select these launches
         e[0].record(stream)
         solver.smooth(0, uu, b, 0)
         e[1].record(stream)
@@ -656,6 +657,7 @@ def main():
         solver.smooth(0, uu, b, nsw)
         e[3].record(stream)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
         sweep_ms = (e[2].elapsed_time(e[3]) - e[0].elapsed_time(e[1])) / nsw
         flops = 12.0 * dofs  # 6 FMA per DOF: u <- (1 - w) u + b' + sum of 5 scaled neighbours
         bytes_alg = 24.0 * dofs  # read u, b; write u (FP64)
