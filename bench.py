@@ -539,6 +539,7 @@ def timed_variant(pkg, w, k, c, q, u, precision, args, stream, world, rooflines=
                       "k_ins": float(w["simp"][0]) if w.get("simp") is not None else None, "tol": TOL},
            "precision": precision, "value": world * dofs / (ms2 * 1e-3), "unit": "DOF/s", "ms_per_step": ms2,
            "cycles": st2[-1][1], "relres": st2[-1][2], "levels": s2.num_levels,
+           "fine_sweep_dofs_per_s": world * dofs * st2[-1][1] * 2 * s2.opts.nu / (ms2 * 1e-3),
            "converged": all(x[0] == "ok" and x[2] < TOL for x in st2),
            "dtype": "f64" if precision == "fp64" else "f32+f64", **precision_opts(args, precision)}
     if precision == "mixed" and rooflines:
@@ -613,6 +614,7 @@ def main():
     ms_per_step = ms / args.steps
     value = whole_job_rate(dofs * args.steps, world, ms * 1e-3)
     cycles = statuses[-1][1]
+    fine_sweeps = world * dofs * cycles * 2 * solver.opts.nu / (ms_per_step * 1e-3)
     relres = statuses[-1][2]
     ok = all(s[0] == "ok" and s[2] < TOL for s in statuses)
     check = rank == 0 and world == 1 and not args.no_cpu_baseline
@@ -752,6 +754,7 @@ def main():
                        "relres": relres, "converged": ok, "setup_ms": setup_ms,
                        "l2": "no flush: every vector (%d MB) exceeds the 129 MB L2" % (dofs * 8 // 2 ** 20),
                        "parallelism": "replicas" if world > 1 else "single"},
+            "fine_sweep_dofs_per_s": fine_sweeps,
             "clocks": clocks, "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline,
             "cpu_baseline": cpu, "variant": variant, "variant_same_field": variant_same_field,
             "other_configs": other_configs,

@@ -88,7 +88,9 @@ def replay(server, requests, fields, speed=1.0, **opts):
     """Submit requests at their arrival times (seconds / speed after the first) and wait.
 
     fields(req) -> (k, c) host arrays.  Returns (results, summary) with latency = finish -
-    arrival on the server clock, p50/p99 in seconds and DOF/s = total DOFs / makespan.
+    arrival on the server clock, p50/p99 in seconds, DOF/s = total DOFs / makespan, and the
+    finest-level sweep rate = sum of DOFs x cycles x 2 nu / makespan (the smoothing work
+    done, comparable across requests that need different numbers of cycles and sweeps).
     """
     t0 = server.now()
     a0 = requests[0]["arrival"] if requests else 0.0
@@ -108,9 +110,13 @@ def replay(server, requests, fields, speed=1.0, **opts):
     dofs = np.array([(r["N"] + 1) * (r["NT"] + 1) for r in requests], dtype=np.float64)
     span = max(x["t_end"] for x in res) - min(x["t_submit"] for x in res)
     nu0 = opts.get("nu")
+    # smoothing work on the finest level: 2 nu sweeps per V-cycle (the nu of the attempt that
+    # returned, so an escalated request's first attempt is not counted)
+    sweeps = sum(d * x["cycles"] * 2 * x["nu"] for d, x in zip(dofs, res))
     summary = dict(requests=len(res), ok=sum(x["status"] == "ok" for x in res),
                    nu_raised=sum(1 for x in res if nu0 and x["nu"] > nu0),
                    p50_s=float(np.percentile(lat, 50)), p99_s=float(np.percentile(lat, 99)),
                    dofs_per_s=float(dofs.sum() / span), makespan_s=float(span),
+                   fine_sweep_dofs_per_s=float(sweeps / span),
                    mean_cycles=float(np.mean([x["cycles"] for x in res])), peak_bytes=int(server.peak_bytes))
     return res, summary
