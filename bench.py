@@ -144,6 +144,32 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+class BusySampler(ClockSampler):
+    """nvidia-smi utilization.gpu (the share of each sample period in which a kernel ran)."""
+
+    Q = "utilization.gpu"
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        vals = []
+        for ln in self.lines:
+            try:
+                vals.append(float(ln.split(",")[0]))
+            except ValueError:
+                continue
+        if not vals:
+            return None
+        return {"median_pct": statistics.median(vals), "mean_pct": sum(vals) / len(vals), "samples": len(vals),
+                "what": "nvidia-smi utilization.gpu every 100 ms over the closed-loop replay: the share of "
+                        "time in which at least one kernel ran (not how many SMs it used)"}
+
+
 def gpu_smi_id(dev):
     import torch
 
@@ -394,7 +420,7 @@ def mixed_rooflines(solver, stream, wname, dofs, nu, reps=20):
     return out
 
 
-def run_serving(nreq, workers, compare=8):
+def run_serving(nreq, workers, compare=8, gpu_id=None):
     """Closed loop (all requests queued at once) for throughput, then the same requests
     with their Poisson gaps rescaled to 0.5x, 0.8x and 1.0x that throughput for latency
     (0.8x is the headline p50/p99)."""
@@ -406,7 +432,12 @@ def run_serving(nreq, workers, compare=8):
     opts = dict(SERVING_OPTS)
     with sv.Server(workers=workers, max_nu=SERVING_MAX_NU) as srv:
         sv.replay(srv, reqs[: min(4, nreq)], fields, speed=1e9, **opts)  # warm-up
+        busy = BusySampler(gpu_id) if gpu_id is not None else None
+        if busy:
+            busy.start()
         _, closed = sv.replay(srv, reqs, fields, speed=1e9, **opts)
+        if busy:
+            closed["gpu_busy"] = busy.stop()
         rate = closed["requests"] / closed["makespan_s"]  # requests per second
         mean_gap = (reqs[-1]["arrival"] - reqs[0]["arrival"]) / max(1, len(reqs) - 1)
         loads = {}
@@ -736,7 +767,7 @@ def main():
         del u, q
         solver.close()
         torch.cuda.empty_cache()
-        serving = run_serving(args.serving_requests, args.serving_workers)
+        serving = run_serving(args.serving_requests, args.serving_workers, gpu_id=gpu_smi_id(dev))
 
     cpu = None
     if check:
