@@ -473,6 +473,30 @@ def test_full_size_filtered_simp_against_exact_solution(workload, precision):
     g.close()
 
 
+@pytest.mark.parametrize("workload,precision", [("filtered_simp", "fp64"), ("filtered_simp", "mixed"),
+                                                ("filtered_simp_high_contrast", "mixed")])
+def test_full_size_adjoint_against_exact_solution(workload, precision):
+    """The adjoint solve (Sec. 7.1: J^T lam = b dt / Theta_ref, Theta_ref = 1) of the 4096 x
+    16384 workloads in the benchmark's launch configuration, solved to relative residual
+    1e-8 and checked against the oracle's exact backward time stepping to the same bars as
+    the forward solve: 1e-10 in FP64, 1e-8 in mixed precision."""
+    w = getattr(wl, workload)()
+    N, NT, L, tT = w["N"], w["NT"], w["L"], w["tT"]
+    ko, co = oracle.simp(w["chi"], w["simp"])
+    g = pkg.Solver(N, NT, L, tT, T(ko), T(co), precision=precision, tol=1e-8)
+    b = torch.empty((NT + 1, N + 1), dtype=torch.float64, device=DEV)
+    g.assemble_load(T(w["q"]), b)
+    lam = torch.empty_like(b)
+    st, cyc, rr = g.solve_adjoint(lam, b * g.dt)
+    assert st == "ok" and rr < 1e-8, (st, cyc, rr)
+    bo = oracle.assemble_load(N, NT, L / N, w["q"])
+    le = oracle.exact(N, NT, L, tT, ko, co, bo * (tT / NT), adj=True)
+    err = rel(N_(lam), le)
+    print("%s %s adjoint: cycles %d relres %.3e max rel err vs exact %.3e" % (w["name"], precision, cyc, rr, err))
+    assert err < (1e-10 if precision == "fp64" else 1e-8), err
+    g.close()
+
+
 @pytest.mark.parametrize("i,interp,nu", [(0, "C", 5), (2, "C", 5), (2, "B", 5), (3, "C", 10)])
 @pytest.mark.parametrize("adj", [False, True])
 def test_mixed_solve_loop_matches_repeated_vcycles(i, interp, nu, adj):
