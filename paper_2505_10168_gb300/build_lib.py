@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libstmg.so")
 OBJDIR = os.path.join(HERE, "_build")
-SOURCES = ["stmg_host.cu", "stmg_kernels.cu", "stmg_stream.cu", "stmg_slab.cu", "stmg_server.cu", "stmg_noalloc.cu", "stmg_galerkin.cu"]
+SOURCES = ["stmg_host.cu", "stmg_kernels.cu", "stmg_stream.cu", "stmg_stream_down.cu", "stmg_slab.cu", "stmg_server.cu", "stmg_noalloc.cu", "stmg_galerkin.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "-I" + INCLUDE, "-I" + CSRC]
 

@@ -41,5 +41,8 @@ void stream_layout(int N, int NT, int own, long long resident_warps, StreamArgs&
 // S sweeps in one pass of the given mode (1..5 for the DOWN modes, 1..8 for the plain and
 // UP modes); adj selects J^T.
 cudaError_t launch_stream(int mode, bool adj, int S, const StreamArgs& a, cudaStream_t s);
+// The DOWN modes of launch_stream (kStreamDownX, kStreamDownT, kStreamDownTB), in their own
+// translation unit; launch_stream counts the launch.
+cudaError_t launch_stream_down(int mode, bool adj, int S, const StreamArgs& a, cudaStream_t s);
 
 }  // namespace stmg
