@@ -210,15 +210,16 @@ __device__ __forceinline__ Vf<V> stage(float a, const Vf<V>& x, const Vf<V>& px,
 }
 
 // Fields of one ring slot, kQ float4 per lane each (the FP64 iterate: 2 kQ): b', the
-// starting iterate, the coarse correction rows (UP), the FP64 iterate (UP and plain passes).
-template <int MODE>
+// starting iterate, the coarse correction rows (UP), the FP64 iterate (UP and plain passes
+// that add into it; NO64: none of them does, and the slot ends before that field).
+template <int MODE, bool NO64>
 struct Ring {
   static constexpr bool kDown = Width<MODE>::kDown;
   static constexpr int kQ = Width<MODE>::kVec / 4;
   static constexpr bool kHasZ = MODE == 3 || MODE == 4 || MODE == 6;
   static constexpr int kB = 0, kU = kQ, kZ = 2 * kQ, kZB = 3 * kQ;
   static constexpr int k64 = kDown ? 0 : (MODE == 6 ? 4 * kQ : (kHasZ ? 3 * kQ : 2 * kQ));
-  static constexpr int kWidth = kDown ? 2 * kQ : k64 + 2 * kQ;  // float4 per lane and slot
+  static constexpr int kWidth = kDown ? 2 * kQ : (NO64 ? k64 : k64 + 2 * kQ);  // float4 per lane and slot
   static constexpr int kDepth = 4;                               // rows in flight per warp
 };
 
@@ -236,13 +237,16 @@ struct Pipe {
 // MODE: 0 plain sweeps, 1 sweeps + residual + x-restriction, 2 sweeps + residual +
 // causal t-restriction, 3 x-prolongation + sweeps, 4 causal t-prolongation + sweeps,
 // 5 sweeps + residual + bilinear t-restriction, 6 bilinear t-prolongation + sweeps.
-// Z: a DOWN pass compiled for a zero starting iterate, which stages no iterate rows and
-// holds less state (166 registers instead of 196: 12 warps per SM instead of 8); the other
-// instantiations take the flag at run time.
-template <bool ADJ, int S, int MODE, bool Z>
+// LEAN: the pass is compiled without one of its input streams.  A DOWN pass then starts
+// from a zero iterate, stages no iterate rows and holds less state (166 registers instead
+// of 196: 12 warps per SM instead of 8); a plain or UP pass does not add into the FP64
+// iterate, stages no FP64 rows and has a ring slot of 3 fields instead of 5 (x-prolongation;
+// mixed 4096 x 16384 solve 14.75 -> 14.53 ms).  The general instantiations take both
+// choices at run time.
+template <bool ADJ, int S, int MODE, bool LEAN>
 __global__ void __launch_bounds__(Width<MODE>::kThreads, MinBlocks<MODE, S>::value) k_stream(StreamArgs a) {
   static_assert(S >= 1 && S <= Width<MODE>::kMaxS, "sweeps per pass");
-  using R = Ring<MODE>;
+  using R = Ring<MODE, !Width<MODE>::kDown && LEAN>;
   using Wd = Width<MODE>;
   constexpr int kVec = Wd::kVec;
   constexpr int kQ = kVec / 4;
@@ -251,7 +255,8 @@ __global__ void __launch_bounds__(Width<MODE>::kThreads, MinBlocks<MODE, S>::val
   constexpr int kWarpsPerBlock = Wd::kWarpsPerBlock;
   using V = Vf<kVec>;
   constexpr bool DOWN = R::kDown;
-  const bool zero_init = Z || a.zero_init != 0;
+  const bool zero_init = (DOWN && LEAN) || a.zero_init != 0;
+  const bool add64 = !DOWN && !LEAN && a.u64 != nullptr;  // add the result into the FP64 iterate
   constexpr int kD = R::kDepth;
   constexpr int kSlot = R::kWidth * 32;  // float4 per slot
   __shared__ float4 ring[kWarpsPerBlock * kD * kSlot];
@@ -338,7 +343,7 @@ __global__ void __launch_bounds__(Width<MODE>::kThreads, MinBlocks<MODE, S>::val
         cp_async<16>(slot + (R::kZB + q) * 32 + lane, a.z, (size_t)((n >> 1) + 1) * a.pc + col + 4 * q, a.bs,
                      ok && inside && (n & 1));
     }
-    if (!DOWN && a.u64 != nullptr) {
+    if (add64) {
 #pragma unroll
       for (int q = 0; q < 2 * kQ; ++q) cp_async<16>(slot + (R::k64 + q) * 32 + lane, a.u64, ro + 2 * q, a.bs, ok && inside);
     }
@@ -390,7 +395,7 @@ __global__ void __launch_bounds__(Width<MODE>::kThreads, MinBlocks<MODE, S>::val
       else
         out.v[k] = stage<DIR>(a.omc, out.v[k - 1], in.v[k - 1], in.hl[k], in.hr[k], out.hl[k], out.hr[k], b, cf);
     }
-    if (!DOWN && a.u64 != nullptr) {
+    if (add64) {
       double2 acc[kVec / 2];
 #pragma unroll
       for (int q = 0; q < kVec / 2; ++q) {
@@ -478,7 +483,7 @@ __global__ void __launch_bounds__(Width<MODE>::kThreads, MinBlocks<MODE, S>::val
   // built.  The rows come from the kernels before this one: wait for them (a no-op unless
   // this grid was launched ahead of its predecessor's end) and let the next pass launch.
   pdl_wait();
-  if (!DOWN && a.u64 != nullptr) ku = -scale_exp(a.kexp);
+  if (add64) ku = -scale_exp(a.kexp);
 #pragma unroll
   for (int j = 0; j < kD; ++j) fetch(j);
   int j = 0;
@@ -509,14 +514,14 @@ __global__ void __launch_bounds__(Width<MODE>::kThreads, MinBlocks<MODE, S>::val
   cp_wait<0>();
 }
 
-template <bool ADJ, int S, int MODE, bool Z>
-cudaError_t launch_z(const StreamArgs& a0, cudaStream_t s) {
+template <bool ADJ, int S, int MODE, bool LEAN>
+cudaError_t launch_lean(const StreamArgs& a0, cudaStream_t s) {
   // resident blocks per SM of this instantiation (the same on every device of a process)
   static std::atomic<int> resident{0};
   int nb = resident.load(std::memory_order_relaxed);
   if (nb == 0) {
     cudaError_t e =
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stream<ADJ, S, MODE, Z>, Width<MODE>::kThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stream<ADJ, S, MODE, LEAN>, Width<MODE>::kThreads, 0);
     if (e != cudaSuccess) return e;
     nb = nb < 1 ? 1 : nb;
     resident.store(nb, std::memory_order_relaxed);
@@ -532,7 +537,7 @@ cudaError_t launch_z(const StreamArgs& a0, cudaStream_t s) {
   const unsigned grid = (unsigned)((warps + wpb - 1) / wpb);
   // programmatic dependent launch: the pass may start (and load its coefficients) while the
   // previous kernel of the stream drains; it waits for that kernel before touching any row
-  return launch_pdl(k_stream<ADJ, S, MODE, Z>, dim3(grid), dim3(Width<MODE>::kThreads), s, a);
+  return launch_pdl(k_stream<ADJ, S, MODE, LEAN>, dim3(grid), dim3(Width<MODE>::kThreads), s, a);
 }
 
 // Levels of at least this many DOFs take the DOWN kernel that holds the iterate state even
@@ -545,9 +550,11 @@ template <bool ADJ, int S, int MODE>
 cudaError_t launch_k(const StreamArgs& a, cudaStream_t s) {
   if constexpr (Width<MODE>::kDown) {
     if (a.zero_init && (long long)(a.N + 1) * (a.NT + 1) < kZeroStartMaxDofs)
-      return launch_z<ADJ, S, MODE, true>(a, s);
+      return launch_lean<ADJ, S, MODE, true>(a, s);
+  } else {
+    if (a.u64 == nullptr) return launch_lean<ADJ, S, MODE, true>(a, s);
   }
-  return launch_z<ADJ, S, MODE, false>(a, s);
+  return launch_lean<ADJ, S, MODE, false>(a, s);
 }
 
 template <bool ADJ, int MODE>
