@@ -377,15 +377,18 @@ NCU_TRAFFIC = {
     ("4096x16384", "k_defect (FP64, finest level)"): 1.3325e9,
     ("4096x16384", "k_stream UP + FP64 accumulate (finest level)"): 1.7477e9,
     ("4096x16384", "k_stream DOWN from zero (finest level)"): 0.6297e9,
+    # captured on 2048 x 16384 (466.8 MB for 33.57 M DOFs) and scaled by the DOFs
+    ("4096x16384", "k_stream UP into the FP32 iterate (finest level)"): 0.9335e9,
 }
 
 
 def mixed_rooflines(solver, stream, wname, dofs, nu, reps=20):
-    """The mixed scheme's three heaviest steps, each launched alone `reps` times on the
-    solver's stream (after its timed solves) and timed with CUDA events there: the FP64
-    defect (6 FP64 FMA, 20 B per DOF), the finest level's UP pass that adds into the FP64
-    iterate (26 B per DOF) and its DOWN pass from zero (10 B per DOF).  Shares of the solve
-    come from the launch list, not from here."""
+    """The mixed scheme's heaviest steps, each launched alone `reps` times on the solver's
+    stream (after its timed solves) and timed with CUDA events there: the FP64 defect (6 FP64
+    FMA, 20 B per DOF), the finest level's UP pass that adds into the FP64 iterate (26 B per
+    DOF), its UP pass into the FP32 iterate (read u, b', z, write u: 14 B per DOF; the inner
+    cycles' form) and its DOWN pass from zero (10 B per DOF).  Shares of the solve come from
+    the launch list, not from here."""
     import torch
 
     if nu > 5:
@@ -394,6 +397,7 @@ def mixed_rooflines(solver, stream, wname, dofs, nu, reps=20):
     out = []
     for kind, name, nbytes, flops in (("defect", "k_defect (FP64, finest level)", 20.0, 12.0),
                                       ("up", "k_stream UP + FP64 accumulate (finest level)", 26.0, None),
+                                      ("up32", "k_stream UP into the FP32 iterate (finest level)", 14.0, None),
                                       ("down", "k_stream DOWN from zero (finest level)", 10.0, None)):
         # an NVTX range per step, so that a profiler can select these launches alone
         torch.cuda.nvtx.range_push("roofline_" + kind)

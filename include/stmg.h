@@ -260,10 +260,12 @@ stmg_status stmg_vcycle(stmg_t handle, int adjoint, double* u, const double* b);
  * from zero, the residual and the restriction into level l+1), kind 1 = level l's UP half
  * (prolongation of level l+1's correction and the nu post-smoothing sweeps; on level 0 added
  * into the FP64 iterate), kind 2 = the FP64 defect of level 0 (the result is then read
- * from the device's scalars, not returned).  The vectors hold whatever the last solve or
- * V-cycle left in them (zero before the first), and the FP64 iterate is modified.
+ * from the device's scalars, not returned), kind 3 = level l's UP half into the FP32
+ * iterate, on level 0 too (the form of every inner FP32 cycle but the last before a
+ * defect).  The vectors hold whatever the last solve or V-cycle left in them (zero before
+ * the first), and the FP64 iterate is modified.
  * STMG_EINVAL unless the handle is STMG_MIXED with nu > 0, 0 <= level < levels - 1 and
- * kind in 0..2 (kind 2: level 0 only). */
+ * kind in 0..3 (kind 2: level 0 only). */
 stmg_status stmg_mixed_pass(stmg_t handle, int level, int adjoint, int kind);
 
 /* ---- allocation-free sensitivity ------------------------------------------------------ */

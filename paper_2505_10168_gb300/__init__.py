@@ -205,9 +205,10 @@ class Solver:
         B.check(B.lib().stmg_vcycle(self._h, int(adjoint), B.ptr(u), B.ptr(b)), self._h)
         return u
 
-    MIXED_PASS_KINDS = {"down": 0, "up": 1, "defect": 2}
+    MIXED_PASS_KINDS = {"down": 0, "up": 1, "defect": 2, "up32": 3}
 
     def mixed_pass(self, level, kind, adjoint=False):
         """Enqueue one step of the mixed scheme on the solver's own vectors (``kind``: "down",
-        "up" or "defect"), without synchronising: for timing single passes."""
+        "up" (on level 0 into the FP64 iterate), "up32" (into the FP32 iterate) or "defect"),
+        without synchronising: for timing single passes."""
         B.check(B.lib().stmg_mixed_pass(self._h, int(level), int(adjoint), self.MIXED_PASS_KINDS[kind]), self._h)

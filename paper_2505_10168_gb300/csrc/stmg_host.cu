@@ -1608,7 +1608,7 @@ stmg_status stmg_mixed_pass(stmg_t h, int level, int adjoint, int kind) {
   if (h->o.precision != STMG_MIXED || h->o.nu <= 0)
     return fail(h, STMG_EINVAL, "stmg_mixed_pass needs the mixed scheme with nu > 0");
   const int nl = (int)h->lev.size();
-  if (kind < 0 || kind > 2 || level < 0 || level >= nl - 1 || (kind == 2 && level != 0))
+  if (kind < 0 || kind > 3 || level < 0 || level >= nl - 1 || (kind == 2 && level != 0))
     return fail(h, STMG_EINVAL, "stmg_mixed_pass: bad level %d or kind %d", level, kind);
   Level& L = h->lev[level];
   if (kind == 0) {
@@ -1616,6 +1616,7 @@ stmg_status stmg_mixed_pass(stmg_t h, int level, int adjoint, int kind) {
     return down32(h, level, adjoint != 0, true, &cur);
   }
   if (kind == 1) return up32(h, level, adjoint != 0, L.u32, level == 0 ? L.u : nullptr);
+  if (kind == 3) return up32(h, level, adjoint != 0, L.u32, nullptr);
   CK(launch_defect(view<double>(L, h->o.omega), L.cf32, adjoint != 0, L.u, L.b, kexp(h), L.b32, h->partials, h->scal,
                    h->s));
   return STMG_OK;

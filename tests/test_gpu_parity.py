@@ -12,6 +12,7 @@ import torch
 
 import oracle
 import paper_2505_10168_gb300 as pkg
+from paper_2505_10168_gb300 import _binding as B
 from paper_2505_10168_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
@@ -533,14 +534,17 @@ def test_mixed_pass_entry_point():
     b = T(_rand_vec(21, (NT + 1, N + 1)))
     u0 = torch.empty_like(b)
     st0 = g.solve(u0, b=b)
-    for kind in ("down", "up", "defect"):
+    for kind in ("down", "up", "up32", "defect"):
         for adj in (False, True):
             g.mixed_pass(0, kind, adjoint=adj)
     g.mixed_pass(g.num_levels - 2, "up")
+    g.mixed_pass(g.num_levels - 2, "up32")
     torch.cuda.synchronize()
-    for lev, kind in ((g.num_levels - 1, "down"), (1, "defect"), (-1, "up")):
+    for lev, kind in ((g.num_levels - 1, "down"), (1, "defect"), (-1, "up"), (g.num_levels - 1, "up32")):
         with pytest.raises(Exception):
             g.mixed_pass(lev, kind)
+    with pytest.raises(Exception):
+        B.check(B.lib().stmg_mixed_pass(g._h, 0, 0, 4), g._h)
     u1 = torch.empty_like(b)
     assert g.solve(u1, b=b) == st0
     assert torch.equal(u0, u1)
