@@ -545,6 +545,14 @@ def differentiation_leg(pkg, dev, stream, reps=3):
         gerr = float(np.abs(g.cpu().numpy() - go).max() / np.abs(go).max())
         out["steps"][prec] = {"value": 2 * dofs / (ms * 1e-3), "unit": "DOF/s (forward + adjoint)",
                               "ms_per_gradient": ms, "gradient_error_vs_oracle": gerr}
+        if prec == "fp64":
+            # the sequential-in-time competitor on the same grid: exact time stepping of the
+            # forward problem on the GPU (one block, a block-scan Thomas solve per step)
+            row0 = torch.zeros((1, N + 1), dtype=torch.float64, device=dev)
+            ut = torch.empty_like(b)
+            ts_ms, _ = cuda_time(stream, lambda: solver.recompute_slabs(b, row0, NT, ut), reps)
+            out["gpu_time_stepping"] = {"value": dofs / (ts_ms * 1e-3), "unit": "DOF/s", "ms_per_solve": ts_ms,
+                                        "what": "exact forward solve by sequential time stepping on the GPU"}
         solver.close()
     return out
 
