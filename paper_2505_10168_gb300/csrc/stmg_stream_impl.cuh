@@ -237,16 +237,20 @@ struct Pipe {
 // MODE: 0 plain sweeps, 1 sweeps + residual + x-restriction, 2 sweeps + residual +
 // causal t-restriction, 3 x-prolongation + sweeps, 4 causal t-prolongation + sweeps,
 // 5 sweeps + residual + bilinear t-restriction, 6 bilinear t-prolongation + sweeps.
-// LEAN: the pass is compiled without one of its input streams.  A DOWN pass then starts
-// from a zero iterate, stages no iterate rows and holds less state (166 registers instead
-// of 196: 12 warps per SM instead of 8); a plain or UP pass does not add into the FP64
-// iterate, stages no FP64 rows and has a ring slot of 3 fields instead of 5 (x-prolongation;
-// mixed 4096 x 16384 solve 14.75 -> 14.53 ms).  The general instantiations take both
-// choices at run time.
-template <bool ADJ, int S, int MODE, bool LEAN>
+// FORM: which of the pass's run-time choices are fixed when it is compiled, so that the row
+// loop carries no branch on them.
+//   kGeneral  both choices at run time (zero start, FP64 accumulate);
+//   kLean     one input stream fewer: a DOWN pass from a zero iterate (stages no iterate
+//             rows, holds less state: 166 registers instead of 196, 12 warps per SM instead
+//             of 8), or a plain or UP pass that does not add into the FP64 iterate (stages
+//             no FP64 rows, a ring slot of 3 fields instead of 5; mixed 4096 x 16384 solve
+//             14.75 -> 14.53 ms);
+//   kContinue a DOWN pass from the iterate in memory (14.50 -> 14.41 ms).
+enum { kGeneral = 0, kLean = 1, kContinue = 2 };
+template <bool ADJ, int S, int MODE, int FORM>
 __global__ void __launch_bounds__(Width<MODE>::kThreads, MinBlocks<MODE, S>::value) k_stream(StreamArgs a) {
   static_assert(S >= 1 && S <= Width<MODE>::kMaxS, "sweeps per pass");
-  using R = Ring<MODE, !Width<MODE>::kDown && LEAN>;
+  using R = Ring<MODE, !Width<MODE>::kDown && FORM == kLean>;
   using Wd = Width<MODE>;
   constexpr int kVec = Wd::kVec;
   constexpr int kQ = kVec / 4;
@@ -255,8 +259,8 @@ __global__ void __launch_bounds__(Width<MODE>::kThreads, MinBlocks<MODE, S>::val
   constexpr int kWarpsPerBlock = Wd::kWarpsPerBlock;
   using V = Vf<kVec>;
   constexpr bool DOWN = R::kDown;
-  const bool zero_init = (DOWN && LEAN) || a.zero_init != 0;
-  const bool add64 = !DOWN && !LEAN && a.u64 != nullptr;  // add the result into the FP64 iterate
+  const bool zero_init = (DOWN && FORM == kLean) || (FORM != kContinue && a.zero_init != 0);
+  const bool add64 = !DOWN && FORM == kGeneral && a.u64 != nullptr;  // add the result into the FP64 iterate
   constexpr int kD = R::kDepth;
   constexpr int kSlot = R::kWidth * 32;  // float4 per slot
   __shared__ float4 ring[kWarpsPerBlock * kD * kSlot];
@@ -514,14 +518,14 @@ __global__ void __launch_bounds__(Width<MODE>::kThreads, MinBlocks<MODE, S>::val
   cp_wait<0>();
 }
 
-template <bool ADJ, int S, int MODE, bool LEAN>
-cudaError_t launch_lean(const StreamArgs& a0, cudaStream_t s) {
+template <bool ADJ, int S, int MODE, int FORM>
+cudaError_t launch_form(const StreamArgs& a0, cudaStream_t s) {
   // resident blocks per SM of this instantiation (the same on every device of a process)
   static std::atomic<int> resident{0};
   int nb = resident.load(std::memory_order_relaxed);
   if (nb == 0) {
     cudaError_t e =
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stream<ADJ, S, MODE, LEAN>, Width<MODE>::kThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stream<ADJ, S, MODE, FORM>, Width<MODE>::kThreads, 0);
     if (e != cudaSuccess) return e;
     nb = nb < 1 ? 1 : nb;
     resident.store(nb, std::memory_order_relaxed);
@@ -537,7 +541,7 @@ cudaError_t launch_lean(const StreamArgs& a0, cudaStream_t s) {
   const unsigned grid = (unsigned)((warps + wpb - 1) / wpb);
   // programmatic dependent launch: the pass may start (and load its coefficients) while the
   // previous kernel of the stream drains; it waits for that kernel before touching any row
-  return launch_pdl(k_stream<ADJ, S, MODE, LEAN>, dim3(grid), dim3(Width<MODE>::kThreads), s, a);
+  return launch_pdl(k_stream<ADJ, S, MODE, FORM>, dim3(grid), dim3(Width<MODE>::kThreads), s, a);
 }
 
 // Levels of at least this many DOFs take the DOWN kernel that holds the iterate state even
@@ -549,12 +553,12 @@ constexpr long long kZeroStartMaxDofs = 1ll << 23;
 template <bool ADJ, int S, int MODE>
 cudaError_t launch_k(const StreamArgs& a, cudaStream_t s) {
   if constexpr (Width<MODE>::kDown) {
-    if (a.zero_init && (long long)(a.N + 1) * (a.NT + 1) < kZeroStartMaxDofs)
-      return launch_lean<ADJ, S, MODE, true>(a, s);
+    if (!a.zero_init) return launch_form<ADJ, S, MODE, kContinue>(a, s);
+    if ((long long)(a.N + 1) * (a.NT + 1) < kZeroStartMaxDofs) return launch_form<ADJ, S, MODE, kLean>(a, s);
   } else {
-    if (a.u64 == nullptr) return launch_lean<ADJ, S, MODE, true>(a, s);
+    if (a.u64 == nullptr) return launch_form<ADJ, S, MODE, kLean>(a, s);
   }
-  return launch_lean<ADJ, S, MODE, false>(a, s);
+  return launch_form<ADJ, S, MODE, kGeneral>(a, s);
 }
 
 template <bool ADJ, int MODE>
